@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused sufficient-statistics pass on the paper's Table 1 workload.
+
+Workload: Table 1 (arxiv 2604.23826), n = 1e9 rows per GPU, seed 1, generated on
+the device into the L32 columnar layout (60 B/row; A int64, nine int32 columns,
+cotC and J float64).  One step = the whole hot path over the table: the exact
+fused pass (n, s = X^T 1, S = X^T X; bit-exact for the integer-valued columns)
+followed by finalize (mean, covariance, correlation, PCA eigenpairs) and the
+device-to-host read of its result.  Inputs (60 GB) are larger than L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W]        the CUDA path (default N=1)
+  python bench.py --impl reference                       the CPU oracle as the reference arm
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX at stated accuracy vs plain FP64"
+UNIT = "rows/s"
+SEED = 1
+BYTES_PER_ROW = {0: 60, 1: 44}
+
+# DRAM traffic per row of the exact pass, from one ncu capture (see profiles/), with the
+# hash of the kernel sources it was taken on; null when the sources have changed since.
+NCU_TRAFFIC = {"bytes_per_row": None, "src_hash": None}
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("k_exact.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2604_23826_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=float, default=1e9, help="rows per GPU")
+    ap.add_argument("--layout", choices=("L32", "L16"), default="L32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--chunk-rows", type=int, default=1 << 24)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- CPU oracle runs
+def oracle_sample(seconds: float, row0: int = 0):
+    """Time the per-row oracle (exact sums + exact centering + Jacobi) on a sample of
+    Table 1 sized for about `seconds` of CPU work; returns (rows, seconds, threads)."""
+    import oracle as O
+    threads = O.default_threads()
+    t0 = time.perf_counter()
+    O.stats_table1(SEED, 200_000, row0=row0, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(max(200_000 * seconds / dt, 200_000), 2e9))
+    t0 = time.perf_counter()
+    st = O.stats_table1(SEED, n, row0=row0, threads=threads)
+    _, cov, _ = O.analysis_from_stats(st)
+    O.jacobi(cov)
+    return n, time.perf_counter() - t0, threads
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import oracle as O
+    threads = O.default_threads()
+    # size each step for ~8 s of CPU work
+    t0 = time.perf_counter()
+    O.stats_table1(SEED, 200_000, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n_step = int(min(max(200_000 * 8.0 / dt, 200_000), 1e9))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        st = O.stats_table1(SEED, n_step, row0=i * n_step, threads=threads)
+        _, cov, _ = O.analysis_from_stats(st)
+        O.jacobi(cov)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = n_step / (ms / 1000.0)
+    sample = (f"Table 1 rows, seed {SEED}, {n_step} rows per step (a bounded sample of the {int(args.n)}-row "
+              f"workload): per-row exact sums (__int128 / double-double), exact centering, Jacobi")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int128/f64x2", "data": "synthetic",
+           "config": {"workload": f"table1_n{int(args.n)}_seed{SEED}_{args.layout}", "rows_per_step": n_step,
+                      "p": 12, "where": "host CPU cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- the CUDA path
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    layout = G.STATS_T1_L32 if args.layout == "L32" else G.STATS_T1_L16
+    n = int(args.n)
+    bpr = BYTES_PER_ROW[layout]
+    row0 = rank * n  # weak scaling: each rank its own contiguous block of the global table
+    stream = torch.cuda.current_stream()
+
+    # ---- generation (a1), untimed in the metric, reported separately ----
+    cols = G.alloc_table1(n, layout)
+    G.stats_gen_table1(SEED, row0, min(n, 1 << 20), layout, cols)  # warm the generator
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record()
+    G.stats_gen_table1(SEED, row0, n, layout, cols)
+    g1.record()
+    torch.cuda.synchronize()
+    gen_ms = g0.elapsed_time(g1)
+
+    cfg = G.stats_table1_config(layout, row0 + n, G.STATS_EXACT)
+    ctx = G.stats_init(cfg)
+    pass_events = []
+
+    def step(record: bool):
+        G.stats_reset(ctx)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        G.stats_accumulate(ctx, cols, n, stream)
+        if record:
+            e1.record(stream)
+            pass_events.append((e0, e1))
+        return G.stats_finalize(ctx, 0)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in pass_events) / len(pass_events)
+
+    # correctness of what was timed: identifier closed forms of this rank's rows
+    raw = G.stats_raw(ctx)
+    lo, hi = row0, row0 + n
+    checks = {"sumA": raw.s_exact[0] == hi * (hi + 1) // 2 - lo * (lo + 1) // 2,
+              "sumA2": raw.S_exact[0][0] == (hi * (hi + 1) * (2 * hi + 1) - lo * (lo + 1) * (2 * lo + 1)) // 6,
+              "n": raw.n == n}
+
+    # ---- the plain FP64 comparator on the same table (the metric's "vs plain FP64") ----
+    comparator = None
+    if not args.no_comparator:
+        with G.stats_init(G.stats_table1_config(layout, row0 + n, G.STATS_FP64)) as c64:
+            G.stats_accumulate(c64, cols, n, stream)
+            G.stats_sync(c64)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            G.stats_reset(c64)
+            f0.record(stream)
+            G.stats_accumulate(c64, cols, n, stream)
+            f1.record(stream)
+            G.stats_sync(c64)
+            fp64_ms = f0.elapsed_time(f1)
+            r64 = G.stats_raw(c64)
+        import math
+        relA = abs(r64.S[0, 0] - float(raw.S_exact[0][0])) / float(raw.S_exact[0][0])
+        comparator = {"kernel": "plain FP64 CUDA cores (raw moments)", "rows_per_s": n / (fp64_ms / 1e3),
+                      "ms": fp64_ms, "speedup_exact_vs_fp64": fp64_ms / kernel_ms,
+                      "fp64_rel_err_sumA2": relA if math.isfinite(relA) else None}
+
+    # ---- e2e: the same step through host (pinned) buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = n
+        host = None
+        while host is None and n_e2e >= (1 << 24):
+            try:
+                host = [torch.empty(n_e2e, dtype=c.dtype, pin_memory=True) for c in cols]
+            except RuntimeError:
+                host = None
+                n_e2e //= 2
+        if host is not None:
+            for h, c in zip(host, cols):
+                h.copy_(c[:n_e2e])
+            torch.cuda.synchronize()
+
+            def step_e2e():
+                G.stats_reset(ctx)
+                G.stats_accumulate_host(ctx, host, n_e2e, args.chunk_rows, stream)
+                return G.stats_finalize(ctx, 0)
+
+            step_e2e()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            k_e2e = max(2, min(args.steps, 4))
+            h0 = torch.cuda.Event(enable_timing=True)
+            h1 = torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            for _ in range(k_e2e):
+                step_e2e()
+            h1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms = h0.elapsed_time(h1) / k_e2e
+            pa = 11
+            T = 12 * 13 // 2
+            result_bytes = 8 * (1 + 12 + T + 2 * 12 + 2 * T + pa + 3 * pa * pa + pa + 8) + 8 + 4
+            e2e = {"value": n_e2e / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n_e2e * bpr,
+                   "d2h_bytes_per_step": result_bytes, "rows": n_e2e, "ms_per_step": e2e_ms, "steps": k_e2e,
+                   "api": "stats_accumulate_host (pinned host columns, double-buffered chunks) + stats_finalize"}
+            del host
+        else:
+            e2e = {"value": None, "unit": UNIT, "note": "pinned host allocation failed"}
+
+    # ---- reduce over ranks ----
+    t = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ok = torch.tensor([1 if all(checks.values()) else 0], device=dev)
+        dist.all_reduce(ok, op=dist.ReduceOp.MIN)
+        checks["all_ranks"] = bool(ok.item())
+        if e2e and e2e.get("value"):
+            ev = torch.tensor([n_e2e / e2e["value"]], dtype=torch.float64, device=dev)
+            dist.all_reduce(ev, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * n_e2e / ev.item()
+    elapsed_ms, kernel_ms = t.tolist()
+    ms_per_step = elapsed_ms / args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows, secs, threads = oracle_sample(15.0)
+        cpu = {"value": rows / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{rows} Table 1 rows (seed {SEED}) of the {n}-row workload: per-row exact "
+                         f"__int128/double-double sums, exact centering, Jacobi; {secs:.1f} s"}
+
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    achieved = n * bpr / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC["bytes_per_row"] and NCU_TRAFFIC["src_hash"] == kernel_src_hash():
+        traffic = NCU_TRAFFIC["bytes_per_row"] * n
+    out = {
+        "metric": METRIC, "value": world * n / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"table1_n{n:.0e}_seed{SEED}_{args.layout}".replace("+", ""), "rows_per_gpu": n,
+                   "p": 12, "layout": args.layout, "bytes_per_row": bpr, "mode": "STATS_EXACT",
+                   "step": "exact fused pass + finalize (mean, cov, corr, PCA) + D2H of the result",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"rows sharded, {world} replica(s)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src, "traffic": traffic,
+                     "kernel": "exact_pass_kernel<ConvT1>", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes": n * bpr},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "generator": {"rows_per_s": n / (gen_ms / 1e3), "GB_per_s_written": n * bpr / (gen_ms / 1e3) / 1e9},
+        "comparator": comparator,
+        "checks": checks,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

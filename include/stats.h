@@ -1,0 +1,251 @@
+/*
+ * stats.h -- C ABI of the GB300 sufficient-statistics library (libsuffstats.so).
+ *
+ * One streaming pass over a tall-skinny n x p table X, stored column by
+ * column on the device, produces the row count n, the column sums s = X^T 1
+ * and the upper triangle of S = X^T X.  Mean, covariance, correlation and the
+ * PCA eigenpairs are then computed from (n, s, S) alone, without revisiting
+ * the data (arxiv 2604.23826, "Data Representation and Sufficient
+ * Statistics": column sums and the cross-product matrix accumulated in one
+ * pass; "Principal Component Analysis Results": PCA from the aggregated
+ * matrices only).
+ *
+ * Conventions that hold for every call:
+ *   - Return codes only; nothing is thrown across the ABI.  stats_strerror()
+ *     names a code.
+ *   - Device pointers are plain CUDA device addresses of the current device;
+ *     host pointers are ordinary process memory.  The library never frees or
+ *     retains caller memory beyond the documented lifetime.
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Work is enqueued asynchronously; device buffers passed
+ *     in must stay valid until the stream reaches the work (stats_sync()).
+ *   - A ctx is used from one stream at a time: calls on one ctx that overlap
+ *     on the GPU race on its accumulator.
+ *   - A CUDA error inside the library makes the ctx sticky-failed: every later
+ *     call on it returns STATS_ESTATE until it is destroyed.
+ *   - Device-side errors (a value outside its declared range, an expired
+ *     bounded wait) are recorded in the ctx and reported by the next call that
+ *     synchronises with the device (stats_sync, stats_raw, stats_finalize,
+ *     stats_export).  An accumulate call whose kernel detected such an error
+ *     leaves the accumulator unchanged.
+ *   - Packed upper triangle: entry (j, k), j <= k, of a p x p symmetric matrix
+ *     is at index j*p - j*(j-1)/2 + (k - j); T(p) = p*(p+1)/2 entries.
+ *   - Matrices returned by stats_finalize are full, row-major, over the
+ *     "analysis columns": the columns not flagged as identifiers, in order.
+ */
+#ifndef SUFFSTATS_STATS_H
+#define SUFFSTATS_STATS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stats_ctx stats_ctx;
+
+typedef enum {
+  STATS_OK = 0,
+  STATS_EINVAL = 1,     /* bad argument or configuration                           */
+  STATS_ENOMEM = 2,     /* a device or host allocation failed                      */
+  STATS_ECUDA = 3,      /* a CUDA runtime call failed (ctx is now sticky-failed)   */
+  STATS_EOVERFLOW = 4,  /* an exact result does not fit its output type            */
+  STATS_ETIMEOUT = 5,   /* a bounded device-side wait expired                      */
+  STATS_ESTATE = 6,     /* ctx is sticky-failed, or the call is out of order       */
+  STATS_ERANGE = 7      /* a value lay outside the digit field of its declared range */
+} stats_status;
+
+/* Column storage types. */
+typedef enum { STATS_I16 = 0, STATS_I32 = 1, STATS_I64 = 2, STATS_F32 = 3, STATS_F64 = 4 } stats_dtype;
+
+/* Arithmetic of the pass.
+ *   STATS_EXACT        integer-valued columns exact (bit-exact s and S), real-valued
+ *                      columns as 56-bit fixed point of their declared range; tensor
+ *                      cores on 8-bit digits with FP32 accumulation flushed to int64
+ *                      before it can round (all products and partial sums are exact
+ *                      integers below 2^24).  Centering in exact integer arithmetic.
+ *   STATS_FP64         the plain FP64 CUDA-core kernel with raw moments, as in the
+ *                      paper (covariance = (S - s s^T / n) / (n - 1) in FP64).
+ *   STATS_FP64_SHIFTED FP64 CUDA cores on x - c, c = the first row accumulated.
+ *   STATS_BF16X3       FP32 data: x - c split into bf16 h + l; S ~ H^T H + H^T L + L^T H
+ *                      on tensor cores, FP32 accumulation flushed to FP64.
+ *   STATS_BF16X4       as BF16X3 plus L^T L.
+ *   STATS_FP32         FP32 CUDA-core FMA on x - c, flushed to FP64.               */
+typedef enum {
+  STATS_EXACT = 0,
+  STATS_FP64 = 1,
+  STATS_FP64_SHIFTED = 2,
+  STATS_BF16X3 = 3,
+  STATS_BF16X4 = 4,
+  STATS_FP32 = 5
+} stats_mode;
+
+/* Table configuration (arrays are read during stats_init only).
+ *   p             number of columns, 1..STATS_MAX_P
+ *   dtypes        p stats_dtype values
+ *   is_identifier p flags (1 = identifier: kept in s and S, left out of mean, cov,
+ *                 corr and PCA, as the paper drops its row index A); may be NULL
+ *   lo, hi        p declared value bounds, lo <= x <= hi for every value of the
+ *                 column; may be NULL.  STATS_EXACT only: they fix each column's
+ *                 digit field (integers: the bytes needed for [lo, hi]; reals: the
+ *                 binary exponent e with max(|lo|,|hi|) < 2^e, fixed point
+ *                 q = round(x * 2^(P - e)) with 56 bits).  NULL means the full
+ *                 range of the integer dtype; real columns need bounds in STATS_EXACT.
+ *   mode          a stats_mode value                                              */
+typedef struct {
+  int32_t p;
+  const int32_t* dtypes;
+  const uint8_t* is_identifier;
+  const double* lo;
+  const double* hi;
+  int32_t mode;
+} stats_config;
+
+#define STATS_MAX_P 256
+/* Widest digit plan of STATS_EXACT: the ones column plus all digit fields. */
+#define STATS_EXACT_MAX_DIGITS 32
+
+/* A 128-bit two's complement integer: value = hi * 2^64 + lo. */
+typedef struct {
+  uint64_t lo;
+  int64_t hi;
+} stats_i128;
+
+/* Create a ctx on the current device: validates cfg, builds the digit plan
+ * (STATS_EXACT), allocates the device accumulator and the per-call scratch.
+ * *out receives the ctx, owned by the caller until stats_destroy().
+ * Errors: EINVAL (bad p, dtype, mode, bounds; plan wider than
+ * STATS_EXACT_MAX_DIGITS), ENOMEM, ECUDA. */
+stats_status stats_init(stats_ctx** out, const stats_config* cfg);
+
+/* Add nrows rows held on the device to the accumulator: dcols is a HOST array of
+ * p DEVICE pointers, column j holding nrows values of dtypes[j], each pointer
+ * aligned to its element size.  When every pointer is 16-byte aligned the rows
+ * stream through the bulk-copy pipeline; otherwise the same kernel reads them
+ * with plain loads (same results, lower throughput).  nrows may be 0.
+ * Asynchronous on stream.
+ * The single fused pass of the paper's "Data Representation and Sufficient
+ * Statistics" section; partial results of the thread blocks are combined on the
+ * device in a fixed order.  Errors: EINVAL (NULL or misaligned pointer, nrows < 0),
+ * ESTATE, ECUDA; range errors are reported at the next synchronising call. */
+stats_status stats_accumulate(stats_ctx* ctx, const void* const* dcols, int64_t nrows, void* stream);
+
+/* Same from HOST memory: hcols is a host array of p HOST pointers (page-locked
+ * memory gives overlapped copies; pageable memory works but serialises).
+ * Rows are copied in chunks of chunk_rows (0 = library default) into two
+ * library-owned device buffers, the copy of one chunk overlapping the pass over
+ * the previous one (one cudaMemcpyAsync per column per chunk on an internal copy
+ * stream, ordered with events).  Returns once everything is enqueued; the host
+ * buffers must stay valid until stats_sync().  Errors as stats_accumulate, plus
+ * ENOMEM for the staging buffers. */
+stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int64_t nrows, int64_t chunk_rows,
+                                   void* stream);
+
+/* dst += src, entry by entry, for two ctxs with identical configuration: the
+ * combination of partial results from disjoint row subsets that the paper does
+ * across its GPUs.  Exact for STATS_EXACT; FP64 modes add in double-double.
+ * Enqueued on dst's last stream; src must be idle.  Errors: EINVAL (configs
+ * differ), ESTATE. */
+stats_status stats_merge(stats_ctx* dst, const stats_ctx* src);
+
+/* Wait for all work of ctx and return its sticky device status. */
+stats_status stats_sync(stats_ctx* ctx);
+
+/* Zero the accumulator and clear recorded device errors (configuration kept).
+ * Stream-ordered on the ctx's last stream. */
+stats_status stats_reset(stats_ctx* ctx);
+
+/* The sufficient statistics.  Synchronises.  Any output may be NULL.
+ *   n              row count
+ *   s              p column sums, rounded once to double
+ *   S_upper        T(p) entries of X^T X (packed upper), rounded once to double
+ *   s_exact        p exact sums; valid for integer-valued columns in STATS_EXACT
+ *                  (zero elsewhere)
+ *   S_exact_upper  T(p) exact entries; valid where both columns are integer-valued
+ *                  in STATS_EXACT (zero elsewhere)
+ * Errors: EOVERFLOW if an exact integer entry does not fit 128 bits (the double
+ * outputs are still written), ERANGE/ETIMEOUT/ECUDA recorded by earlier work. */
+stats_status stats_raw(stats_ctx* ctx, int64_t* n, double* s, double* S_upper, stats_i128* s_exact,
+                       stats_i128* S_exact_upper);
+
+/* Mean, covariance (divisor n - 1), correlation and eigenpairs over the analysis
+ * columns (p_a = number of columns without the identifier flag), computed on the
+ * device from (n, s, S) only.  Synchronises.  Caller-owned HOST outputs, any may
+ * be NULL: mean[p_a], cov[p_a*p_a], corr[p_a*p_a], evals[p_a] (descending),
+ * evecs[p_a*p_a] (row k = eigenvector k, sign chosen so that its largest-magnitude
+ * component is positive).  pca_on: 0 = eigenpairs of cov, 1 = of corr.  A zero
+ * variance gives NaN correlations in its row and column (the paper's "undefined
+ * correlation values"); eigenpairs of corr are then not computed (NaN).
+ * STATS_EXACT centres exactly (n S - s s^T in integer arithmetic) and rounds once;
+ * STATS_FP64 uses the paper's raw-moment formula in FP64.
+ * Errors: EINVAL (n < 2), and those of stats_raw. */
+stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals, double* evecs,
+                            int32_t pca_on);
+
+/* Checkpoint: serialise the accumulator and configuration into buf (len bytes).
+ * With buf == NULL, *len receives the size needed.  Synchronises.
+ * Errors: EINVAL (buffer too small: *len set to the size needed). */
+stats_status stats_export(stats_ctx* ctx, void* buf, size_t* len);
+
+/* Create a ctx on the current device from a stats_export() image.
+ * Errors: EINVAL (not an image of this library / version), ENOMEM, ECUDA. */
+stats_status stats_import(stats_ctx** out, const void* buf, size_t len);
+
+/* Release the ctx and its device memory (synchronises first). NULL is a no-op. */
+void stats_destroy(stats_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* stats_strerror(stats_status st);
+
+/* Number of analysis columns of ctx (columns without the identifier flag). */
+int32_t stats_num_analysis_columns(const stats_ctx* ctx);
+
+/* Tuning knob for tests and measurement: the number of thread blocks of the
+ * pass kernels (0 = library default, a multiple of the SM count).  Results of
+ * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
+stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
+
+/* ---------------------------------------------------------------------------
+ * The paper's Table 1 workload (section "Background and Motivation", Table 1
+ * "Dataset used in this study"): twelve columns
+ *   A = row identifier 1..n, B = randBetween(3,8), C = randBetween(1,10),
+ *   D = randBetween(1,100), E = int(log C / log B * 100),
+ *   F = round(log D / log B * 10000), G = int(|cos C| * 100),
+ *   H = int(|sin D| * 100), cotC = 1.0 / tan C, I = round(|cotC| * 1000),
+ *   J = |tan D|, K = D / C (integer division)
+ * in this column order.  Row i (0-based) draws its three uniforms with
+ * Philox4x32-10 (Salmon et al., SC'11) at counter (i_lo, i_hi, 0, 0) under key
+ * (seed_lo, seed_hi) and maps a 32-bit word u to lo + floor(u * (hi - lo + 1) / 2^32).
+ * ------------------------------------------------------------------------- */
+
+/* Column storage layouts of the Table 1 table.
+ *   STATS_T1_L32: A int64; B C D E F G H I K int32; cotC J float64 (60 B/row)
+ *   STATS_T1_L16: A int64; F int32; B C D E G H I K int16; cotC J float64 (44 B/row) */
+typedef enum { STATS_T1_L32 = 0, STATS_T1_L16 = 1 } stats_t1_layout;
+
+#define STATS_T1_P 12
+
+/* Fill a stats_config's arrays for Table 1 in the given layout, for tables of at
+ * most max_rows rows (sizes the identifier's digit field): dtypes[12],
+ * is_identifier[12] (A only), lo[12], hi[12] (the ranges the Table 1 formulas
+ * produce).  The caller sets p = 12 and the mode.  Errors: EINVAL. */
+stats_status stats_table1_config(int32_t layout, int64_t max_rows, int32_t* dtypes, uint8_t* is_identifier,
+                                 double* lo, double* hi);
+
+/* Generate rows [row0, row0 + nrows) of Table 1 on the device into dcols (host
+ * array of 12 device pointers in the layout's dtypes, 16-byte aligned; element 0
+ * of each column receives row row0).  Counter-based: the values of a row depend
+ * only on (seed, row index), never on chunking.  Asynchronous on stream.
+ * Errors: EINVAL, ECUDA. */
+stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32_t layout, void* const* dcols,
+                              void* stream);
+
+/* Bytes per row of a Table 1 layout (60 or 44), or 0 for an unknown layout. */
+int32_t stats_table1_row_bytes(int32_t layout);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUFFSTATS_STATS_H */

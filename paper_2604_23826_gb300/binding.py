@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libsuffstats (include/stats.h), same names as the C ABI.
+
+Argument marshalling only: every step of the pass runs in the library's CUDA
+kernels.  PyTorch is used for device memory and streams (plumbing).  If the
+compiled library is missing the import of this module fails loudly; there is
+no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+# ----------------------------------------------------------------------------- constants (stats.h)
+STATS_OK, STATS_EINVAL, STATS_ENOMEM, STATS_ECUDA, STATS_EOVERFLOW, STATS_ETIMEOUT, STATS_ESTATE, STATS_ERANGE = \
+    range(8)
+STATS_I16, STATS_I32, STATS_I64, STATS_F32, STATS_F64 = range(5)
+STATS_EXACT, STATS_FP64, STATS_FP64_SHIFTED, STATS_BF16X3, STATS_BF16X4, STATS_FP32 = range(6)
+STATS_T1_L32, STATS_T1_L16 = 0, 1
+STATS_T1_P = 12
+STATS_MAX_P = 256
+
+_NAMES = {STATS_OK: "STATS_OK", STATS_EINVAL: "STATS_EINVAL", STATS_ENOMEM: "STATS_ENOMEM",
+          STATS_ECUDA: "STATS_ECUDA", STATS_EOVERFLOW: "STATS_EOVERFLOW", STATS_ETIMEOUT: "STATS_ETIMEOUT",
+          STATS_ESTATE: "STATS_ESTATE", STATS_ERANGE: "STATS_ERANGE"}
+
+DTYPE_BYTES = {STATS_I16: 2, STATS_I32: 4, STATS_I64: 8, STATS_F32: 4, STATS_F64: 8}
+T1_NAMES = ("A", "B", "C", "D", "E", "F", "G", "H", "cotC", "I", "J", "K")
+
+
+class StatsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_NAMES.get(code, code)} ({stats_strerror(code)})")
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("dtypes", ctypes.POINTER(ctypes.c_int32)),
+                ("is_identifier", ctypes.POINTER(ctypes.c_uint8)), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int32)]
+
+
+class _I128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libsuffstats.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libsuffstats.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.stats_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Config)]
+    L.stats_accumulate.argtypes = [vp, ctypes.POINTER(vp), i64, vp]
+    L.stats_accumulate_host.argtypes = [vp, ctypes.POINTER(vp), i64, i64, vp]
+    L.stats_merge.argtypes = [vp, vp]
+    L.stats_sync.argtypes = [vp]
+    L.stats_reset.argtypes = [vp]
+    L.stats_raw.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I128), ctypes.POINTER(_I128)]
+    L.stats_finalize.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 5 + [i32]
+    L.stats_export.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.stats_import.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_size_t]
+    L.stats_destroy.argtypes = [vp]
+    L.stats_destroy.restype = None
+    L.stats_strerror.argtypes = [ctypes.c_int]
+    L.stats_strerror.restype = ctypes.c_char_p
+    L.stats_num_analysis_columns.argtypes = [vp]
+    L.stats_num_analysis_columns.restype = i32
+    L.stats_set_grid.argtypes = [vp, i32]
+    L.stats_table1_config.argtypes = [i32, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.stats_gen_table1.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, i32, ctypes.POINTER(vp), vp]
+    L.stats_table1_row_bytes.argtypes = [i32]
+    L.stats_table1_row_bytes.restype = i32
+    for name in ("stats_init", "stats_accumulate", "stats_accumulate_host", "stats_merge", "stats_sync",
+                 "stats_reset", "stats_raw", "stats_finalize", "stats_export", "stats_import", "stats_set_grid",
+                 "stats_table1_config", "stats_gen_table1"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != STATS_OK:
+        raise StatsError(code, where)
+
+
+def stats_strerror(code: int) -> str:
+    return load().stats_strerror(code).decode()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _ptr_array(cols: Sequence) -> ctypes.Array:
+    return (ctypes.c_void_p * len(cols))(*[_ptr(c) for c in cols])
+
+
+# ----------------------------------------------------------------------------- configuration
+@dataclass
+class Config:
+    """Mirror of stats_config."""
+    dtypes: Sequence[int]
+    mode: int = STATS_EXACT
+    is_identifier: Optional[Sequence[int]] = None
+    lo: Optional[Sequence[float]] = None
+    hi: Optional[Sequence[float]] = None
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def p(self) -> int:
+        return len(self.dtypes)
+
+    def c_struct(self) -> _Config:
+        p = self.p
+        dt = (ctypes.c_int32 * p)(*self.dtypes)
+        ident = (ctypes.c_uint8 * p)(*self.is_identifier) if self.is_identifier is not None else None
+        lo = (ctypes.c_double * p)(*self.lo) if self.lo is not None else None
+        hi = (ctypes.c_double * p)(*self.hi) if self.hi is not None else None
+        self._keep = [dt, ident, lo, hi]
+        return _Config(p, dt, ident, lo, hi, self.mode)
+
+
+def stats_table1_config(layout: int = STATS_T1_L32, max_rows: int = 10**10, mode: int = STATS_EXACT) -> Config:
+    """The Table 1 configuration (12 columns, identifier A) of a layout."""
+    dt = (ctypes.c_int32 * 12)()
+    ident = (ctypes.c_uint8 * 12)()
+    lo = (ctypes.c_double * 12)()
+    hi = (ctypes.c_double * 12)()
+    _check(load().stats_table1_config(layout, max_rows, dt, ident, lo, hi), "stats_table1_config")
+    return Config(list(dt), mode, list(ident), list(lo), list(hi))
+
+
+def stats_table1_row_bytes(layout: int) -> int:
+    return load().stats_table1_row_bytes(layout)
+
+
+# ----------------------------------------------------------------------------- context
+class Ctx:
+    """Owning handle of a stats_ctx (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle: int, p: int, mode: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.p = p
+        self.mode = mode
+
+    def close(self):
+        if self.handle:
+            load().stats_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def stats_init(cfg: Config) -> Ctx:
+    h = ctypes.c_void_p()
+    s = cfg.c_struct()
+    _check(load().stats_init(ctypes.byref(h), ctypes.byref(s)), "stats_init")
+    return Ctx(h.value, cfg.p, cfg.mode)
+
+
+def stats_accumulate(ctx: Ctx, dcols: Sequence, nrows: int, stream=None):
+    """Add nrows device-resident rows (dcols: tensors or device addresses)."""
+    arr = _ptr_array(dcols)
+    _check(load().stats_accumulate(ctx.handle, arr, nrows, _stream_handle(stream)), "stats_accumulate")
+
+
+def stats_accumulate_host(ctx: Ctx, hcols: Sequence, nrows: int, chunk_rows: int = 0, stream=None):
+    """Add nrows host-resident rows (hcols: pinned tensors / numpy arrays / host addresses)."""
+    arr = _ptr_array(hcols)
+    _check(load().stats_accumulate_host(ctx.handle, arr, nrows, chunk_rows, _stream_handle(stream)),
+           "stats_accumulate_host")
+
+
+def stats_merge(dst: Ctx, src: Ctx):
+    _check(load().stats_merge(dst.handle, src.handle), "stats_merge")
+
+
+def stats_sync(ctx: Ctx):
+    _check(load().stats_sync(ctx.handle), "stats_sync")
+
+
+def stats_reset(ctx: Ctx):
+    _check(load().stats_reset(ctx.handle), "stats_reset")
+
+
+def stats_set_grid(ctx: Ctx, blocks: int):
+    _check(load().stats_set_grid(ctx.handle, blocks), "stats_set_grid")
+
+
+def stats_num_analysis_columns(ctx: Ctx) -> int:
+    return load().stats_num_analysis_columns(ctx.handle)
+
+
+def _i128(v: _I128) -> int:
+    return (int(v.hi) << 64) + int(v.lo)
+
+
+@dataclass
+class Raw:
+    n: int
+    s: np.ndarray           # p, rounded once to double
+    S: np.ndarray           # p x p symmetric, rounded once to double
+    s_exact: list           # p Python ints (exact for integer-valued columns in STATS_EXACT)
+    S_exact: list           # p x p Python ints (exact where both columns are integer-valued)
+    status: int
+
+
+def stats_raw(ctx: Ctx, allow_overflow: bool = False) -> Raw:
+    p = ctx.p
+    T = p * (p + 1) // 2
+    n = ctypes.c_int64()
+    s = np.zeros(p)
+    Su = np.zeros(T)
+    se = (_I128 * p)()
+    Se = (_I128 * T)()
+    rc = load().stats_raw(ctx.handle, ctypes.byref(n), s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          Su.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), se, Se)
+    if rc != STATS_OK and not (allow_overflow and rc == STATS_EOVERFLOW):
+        raise StatsError(rc, "stats_raw")
+    S = np.zeros((p, p))
+    SE = [[0] * p for _ in range(p)]
+    t = 0
+    for j in range(p):
+        for k in range(j, p):
+            S[j, k] = S[k, j] = Su[t]
+            SE[j][k] = SE[k][j] = _i128(Se[t])
+            t += 1
+    return Raw(int(n.value), s, S, [_i128(v) for v in se], SE, rc)
+
+
+@dataclass
+class Analysis:
+    mean: np.ndarray
+    cov: np.ndarray
+    corr: np.ndarray
+    evals: np.ndarray
+    evecs: np.ndarray   # row k = eigenvector k
+
+
+def stats_finalize(ctx: Ctx, pca_on: int = 0) -> Analysis:
+    pa = stats_num_analysis_columns(ctx)
+    mean = np.zeros(pa)
+    cov = np.zeros((pa, pa))
+    corr = np.zeros((pa, pa))
+    ev = np.zeros(pa)
+    V = np.zeros((pa, pa))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    _check(load().stats_finalize(ctx.handle, dp(mean), dp(cov), dp(corr), dp(ev), dp(V), pca_on), "stats_finalize")
+    return Analysis(mean, cov, corr, ev, V)
+
+
+def stats_export(ctx: Ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(load().stats_export(ctx.handle, None, ctypes.byref(n)), "stats_export(size)")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().stats_export(ctx.handle, buf, ctypes.byref(n)), "stats_export")
+    return buf.raw[: n.value]
+
+
+def stats_import(blob: bytes, p: int, mode: int) -> Ctx:
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().stats_import(ctypes.byref(h), buf, len(blob)), "stats_import")
+    return Ctx(h.value, p, mode)
+
+
+def stats_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def stats_gen_table1(seed: int, row0: int, nrows: int, layout: int, dcols: Sequence, stream=None):
+    arr = _ptr_array(dcols)
+    _check(load().stats_gen_table1(seed, row0, nrows, layout, arr, _stream_handle(stream)), "stats_gen_table1")
+
+
+# ----------------------------------------------------------------------------- Table 1 buffers
+def table1_torch_dtypes(layout: int):
+    import torch
+    m = {STATS_I16: torch.int16, STATS_I32: torch.int32, STATS_I64: torch.int64, STATS_F32: torch.float32,
+         STATS_F64: torch.float64}
+    cfg = stats_table1_config(layout, 1)
+    return [m[d] for d in cfg.dtypes]
+
+
+def alloc_table1(nrows: int, layout: int = STATS_T1_L32, device="cuda", pin_memory: bool = False):
+    """Twelve column tensors of a Table 1 layout (torch provides the memory)."""
+    import torch
+    return [torch.empty(max(nrows, 1), dtype=dt, device=device, pin_memory=pin_memory and device == "cpu")
+            for dt in table1_torch_dtypes(layout)]
+
+
+def gen_table1(seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0, cols=None, stream=None):
+    """Generate Table 1 rows on the current device; returns the column tensors."""
+    if cols is None:
+        cols = alloc_table1(nrows, layout)
+    stats_gen_table1(seed, row0, nrows, layout, cols, stream)
+    return cols

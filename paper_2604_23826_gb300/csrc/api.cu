@@ -1,0 +1,793 @@
+// api.cu -- the C ABI of libsuffstats (declared in include/stats.h): context
+// management, the digit plan of the exact pass, launches, host-streamed double
+// buffering, merge, checkpoint.  Every step of the pass itself runs in the
+// kernels of k_exact.cu / k_fp64.cu / k_finalize.cu; this file only validates
+// arguments, owns device memory and orders work on streams.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/stats.h"
+#include "kernels.h"
+
+using namespace ss;
+
+namespace {
+
+constexpr uint64_t kMagic = 0x3130535441545353ull;  // "SSTATS01"
+constexpr int64_t kDefaultChunkRows = int64_t(1) << 24;
+
+struct ColPlan {
+  int k = 0;         // digit bytes
+  int is_signed = 0;
+  int is_real = 0;
+  int shift = 0;     // real: q = RN(x * 2^shift)
+  int emax = 0;      // real: largest allowed biased exponent field
+  int off = 0;       // first digit slot
+};
+
+}  // namespace
+
+struct stats_ctx {
+  int device = 0;
+  int p = 0;
+  int pa = 0;
+  int mode = 0;
+  std::vector<int32_t> dtypes;
+  std::vector<uint8_t> ident;
+  std::vector<double> lo, hi;
+  bool has_bounds = false;
+  // exact plan
+  std::vector<ColPlan> plan;
+  int conv = CONV_GENERIC;
+  ExactParams xp{};  // launch template (pointers of the call filled per launch)
+  int stages = 3;
+  // device state
+  long long* d_g = nullptr;             // EXACT accumulator, kDigits^2
+  unsigned long long* d_call = nullptr; // scratch: per-call accumulator
+  unsigned int* d_ticket = nullptr;     // scratch
+  unsigned int* d_err = nullptr;        // scratch
+  unsigned int* d_status = nullptr;     // sticky device status bits
+  double* d_fs = nullptr;               // FP64: s, s_lo, S, S_lo, shift (one allocation)
+  double* d_fs_lo = nullptr;
+  double* d_fS = nullptr;
+  double* d_fS_lo = nullptr;
+  double* d_shift = nullptr;
+  long long* d_fn = nullptr;
+  double* d_slots = nullptr;            // FP64 scratch: block slots + ticket
+  int slot_grid = 0;
+  bool shift_set = false;
+  double* d_out = nullptr;              // finalize result
+  double* d_work = nullptr;             // finalize scratch
+  double* h_out = nullptr;              // pinned host copy of the result
+  FinalLayout lay{};
+  // host streaming
+  void* d_stage[2] = {nullptr, nullptr};
+  int64_t stage_rows = 0;
+  std::vector<size_t> stage_off;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  cudaStream_t last = nullptr;
+  int grid = 0;
+  int sms = 0;
+  stats_status sticky = STATS_OK;
+};
+
+namespace {
+
+stats_status cuda_fail(stats_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return STATS_OK;
+  if (c) c->sticky = STATS_ECUDA;
+  return STATS_ECUDA;
+}
+
+#define CK(c, expr)                                  \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return cuda_fail(c, _e);  \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int bitlen_u(unsigned long long v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+// Digit field of an integer column with lo <= x <= hi (or the dtype's full range).
+bool int_field(int32_t dt, bool bounded, double lo, double hi, ColPlan& cp) {
+  if (!bounded) {
+    cp.k = dtype_bytes(dt);
+    cp.is_signed = 1;
+    return true;
+  }
+  if (!(lo <= hi) || !isfinite(lo) || !isfinite(hi)) return false;
+  const double ilo = ceil(lo), ihi = floor(hi);
+  if (ilo >= 0) {
+    if (ihi >= 18446744073709551616.0) return false;
+    const int bits = bitlen_u(static_cast<unsigned long long>(std::max(ihi, 0.0)));
+    cp.k = std::max(1, (bits + 7) / 8);
+    cp.is_signed = 0;
+  } else {
+    const double m = std::max(-ilo - 1.0, ihi);
+    if (m >= 9223372036854775808.0) return false;
+    const int bits = bitlen_u(static_cast<unsigned long long>(std::max(m, 0.0))) + 1;
+    cp.k = std::max(1, (bits + 7) / 8);
+    cp.is_signed = 1;
+  }
+  cp.k = std::min(cp.k, dtype_bytes(dt));
+  if (cp.k == dtype_bytes(dt)) cp.is_signed = 1;  // a full-width field is the dtype's own two's complement
+  return true;
+}
+
+// Fixed-point field of a real column with |x| <= max(|lo|, |hi|) < 2^e.
+bool real_field(bool bounded, double lo, double hi, ColPlan& cp) {
+  if (!bounded || !isfinite(lo) || !isfinite(hi) || !(lo <= hi)) return false;
+  const double m = std::max(fabs(lo), fabs(hi));
+  if (!(m > 0)) return false;
+  int e = 0;
+  frexp(m, &e);  // m = f * 2^e, f in [0.5, 1): m < 2^e
+  cp.is_real = 1;
+  cp.k = 7;
+  cp.is_signed = lo < 0 ? 1 : 0;
+  const int P = cp.is_signed ? 8 * cp.k - 2 : 8 * cp.k - 1;
+  cp.shift = P - e;
+  cp.emax = 1022 + e;
+  return true;
+}
+
+bool is_t1_plan(const stats_ctx* c, int layout) {
+  if (c->p != 12) return false;
+  static const int32_t l32[12] = {I64, I32, I32, I32, I32, I32, I32, I32, F64, I32, F64, I32};
+  static const int32_t l16[12] = {I64, I16, I16, I16, I16, I32, I16, I16, F64, I16, F64, I16};
+  const int32_t* want = layout ? l16 : l32;
+  for (int j = 0; j < 12; ++j)
+    if (c->dtypes[j] != want[j]) return false;
+  const auto& P = c->plan;
+  for (int j : {1, 2, 3, 4, 6, 7, 11})
+    if (P[j].is_signed || P[j].k != 1) return false;
+  for (int j : {5, 9})
+    if (P[j].is_signed || P[j].k > 2) return false;
+  if (P[0].is_signed || P[0].k > 5) return false;
+  if (!P[8].is_real || !P[8].is_signed) return false;
+  if (!P[10].is_real || P[10].is_signed) return false;
+  return true;
+}
+
+void set_t1_offsets(stats_ctx* c) {
+  // slots: 0 ones | 1 B | 2 C | 3 D | 4 E | 5 G | 6 H | 7 K | 8-9 F | 10-11 I | 12-16 A | 17-23 cotC | 24-30 J
+  static const int off[12] = {12, 1, 2, 3, 4, 8, 5, 6, 17, 10, 24, 7};
+  static const int k[12] = {5, 1, 1, 1, 1, 2, 1, 1, 7, 2, 7, 1};
+  for (int j = 0; j < 12; ++j) {
+    c->plan[j].off = off[j];
+    c->plan[j].k = k[j];
+  }
+}
+
+stats_status build_plan(stats_ctx* c) {
+  c->plan.assign(c->p, ColPlan{});
+  for (int j = 0; j < c->p; ++j) {
+    const int32_t dt = c->dtypes[j];
+    ColPlan& cp = c->plan[j];
+    if (dt == F32 || dt == F64) {
+      if (!real_field(c->has_bounds, c->has_bounds ? c->lo[j] : 0, c->has_bounds ? c->hi[j] : 0, cp))
+        return STATS_EINVAL;
+    } else if (!int_field(dt, c->has_bounds, c->has_bounds ? c->lo[j] : 0, c->has_bounds ? c->hi[j] : 0, cp)) {
+      return STATS_EINVAL;
+    }
+  }
+  if (is_t1_plan(c, 0) || is_t1_plan(c, 1)) {
+    c->conv = is_t1_plan(c, 0) ? CONV_T1_L32 : CONV_T1_L16;
+    set_t1_offsets(c);
+    return STATS_OK;
+  }
+  if (c->p > kMaxCols) return STATS_EINVAL;
+  int slot = 1;
+  for (int j = 0; j < c->p; ++j) {
+    c->plan[j].off = slot;
+    slot += c->plan[j].k;
+  }
+  if (slot > kDigits) return STATS_EINVAL;
+  c->conv = CONV_GENERIC;
+  // generic pair plan
+  int8_t col[kDigits], byt[kDigits], sg[kDigits];
+  for (int s = 0; s < kDigits; ++s) {
+    col[s] = -2;
+    byt[s] = 0;
+    sg[s] = 0;
+  }
+  col[0] = -1;
+  for (int j = 0; j < c->p; ++j)
+    for (int a = 0; a < c->plan[j].k; ++a) {
+      col[c->plan[j].off + a] = static_cast<int8_t>(j);
+      byt[c->plan[j].off + a] = static_cast<int8_t>(a);
+      sg[c->plan[j].off + a] = (c->plan[j].is_signed && a == c->plan[j].k - 1) ? 1 : 0;
+    }
+  for (int q = 0; q < kDigitPairs; ++q) {
+    c->xp.pc0[q] = col[2 * q];
+    c->xp.pb0[q] = byt[2 * q];
+    c->xp.ps0[q] = sg[2 * q];
+    c->xp.pc1[q] = col[2 * q + 1];
+    c->xp.pb1[q] = byt[2 * q + 1];
+    c->xp.ps1[q] = sg[2 * q + 1];
+  }
+  return STATS_OK;
+}
+
+stats_status check_sticky(const stats_ctx* c) {
+  if (!c) return STATS_EINVAL;
+  return c->sticky != STATS_OK ? STATS_ESTATE : STATS_OK;
+}
+
+stats_status device_status(stats_ctx* c) {
+  unsigned int bits = 0;
+  CK(c, cudaMemcpy(&bits, c->d_status, sizeof(bits), cudaMemcpyDeviceToHost));
+  if (bits & DEV_ETIMEOUT) return STATS_ETIMEOUT;
+  if (bits & DEV_ERANGE) return STATS_ERANGE;
+  if (bits & DEV_EOVERFLOW) return STATS_EOVERFLOW;
+  return STATS_OK;
+}
+
+int default_grid(stats_ctx* c) {
+  if (c->grid > 0) return c->grid;
+  if (c->mode == STATS_EXACT) {
+    int per = exact_max_active_blocks(c->conv, c->stages, c->xp.stage_bytes);
+    if (per < 1) per = 1;
+    return c->sms * per;
+  }
+  return c->sms * 2;
+}
+
+stats_status ensure_slots(stats_ctx* c, int grid) {
+  if (c->d_slots && c->slot_grid >= grid) return STATS_OK;
+  if (c->d_slots) CK(c, cudaFree(c->d_slots));
+  c->d_slots = nullptr;
+  const size_t n = fp64_slot_doubles(grid);
+  CK(c, cudaMalloc(&c->d_slots, n * sizeof(double)));
+  CK(c, cudaMemset(c->d_slots, 0, n * sizeof(double)));
+  c->slot_grid = grid;
+  return STATS_OK;
+}
+
+stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
+  if (nrows == 0) return STATS_OK;
+  const int grid = default_grid(c);
+  if (c->mode == STATS_EXACT) {
+    ExactParams P = c->xp;
+    P.direct = 0;
+    for (int j = 0; j < c->p; ++j) {
+      P.cols[j] = dcols[j];
+      if (!aligned16(dcols[j])) P.direct = 1;
+    }
+    P.nrows = nrows;
+    P.nmain = P.direct ? nrows : (nrows & ~int64_t(7));
+    const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
+    int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
+    CK(c, launch_exact(P, c->conv, g, st));
+  } else {
+    Fp64Params P{};
+    for (int j = 0; j < c->p; ++j) {
+      P.cols[j] = dcols[j];
+      P.dtype[j] = c->dtypes[j];
+    }
+    P.p = c->p;
+    P.nrows = nrows;
+    if (c->mode == STATS_FP64_SHIFTED) {
+      if (!c->shift_set) {
+        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, c->d_shift, st));
+        c->shift_set = true;
+      }
+      P.shift = c->d_shift;
+    }
+    stats_status s = ensure_slots(c, grid);
+    if (s != STATS_OK) return s;
+    P.slots = c->d_slots;
+    P.acc_s = c->d_fs;
+    P.acc_s_lo = c->d_fs_lo;
+    P.acc_S = c->d_fS;
+    P.acc_S_lo = c->d_fS_lo;
+    P.acc_n = c->d_fn;
+    CK(c, launch_fp64(P, grid, st));
+  }
+  c->last = st;
+  return STATS_OK;
+}
+
+stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
+  FinalParams F{};
+  F.p = c->p;
+  F.mode = c->mode == STATS_EXACT ? 0 : 1;
+  F.pca_on = pca_on;
+  F.want_pca = want_pca;
+  for (int j = 0; j < c->p; ++j) {
+    F.col[j].off = c->plan.empty() ? 0 : c->plan[j].off;
+    F.col[j].k = c->plan.empty() ? 0 : c->plan[j].k;
+    F.col[j].shift = c->plan.empty() ? 0 : c->plan[j].shift;
+    F.col[j].is_real = c->plan.empty() ? 0 : c->plan[j].is_real;
+    F.col[j].is_ident = c->ident[j];
+  }
+  F.g = c->d_g;
+  F.fs = c->d_fs;
+  F.fs_lo = c->d_fs_lo;
+  F.fS = c->d_fS;
+  F.fS_lo = c->d_fS_lo;
+  F.fn = c->d_fn;
+  F.shift = (c->mode == STATS_FP64_SHIFTED && c->shift_set) ? c->d_shift : nullptr;
+  F.out = c->d_out;
+  F.work = c->d_work;
+  cudaStream_t st = c->last;
+  CK(c, launch_finalize(F, st));
+  CK(c, cudaMemcpyAsync(c->h_out, c->d_out, c->lay.total * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(c, cudaStreamSynchronize(st));
+  return STATS_OK;
+}
+
+void free_ctx(stats_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_g);
+  cudaFree(c->d_call);
+  cudaFree(c->d_fs);
+  cudaFree(c->d_slots);
+  cudaFree(c->d_out);
+  cudaFree(c->d_work);
+  if (c->h_out) cudaFreeHost(c->h_out);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->d_stage[b]);
+    if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
+    if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  delete c;
+}
+
+stats_status create(stats_ctx** out, const stats_config* cfg) {
+  if (!out || !cfg) return STATS_EINVAL;
+  *out = nullptr;
+  if (cfg->p < 1 || cfg->p > STATS_MAX_P || !cfg->dtypes) return STATS_EINVAL;
+  if (cfg->mode < STATS_EXACT || cfg->mode > STATS_FP32) return STATS_EINVAL;
+  if ((cfg->lo == nullptr) != (cfg->hi == nullptr)) return STATS_EINVAL;
+  // modes not built yet: BF16X3 / BF16X4 / FP32
+  if (cfg->mode == STATS_BF16X3 || cfg->mode == STATS_BF16X4 || cfg->mode == STATS_FP32) return STATS_EINVAL;
+  if ((cfg->mode == STATS_FP64 || cfg->mode == STATS_FP64_SHIFTED) && cfg->p > 12) return STATS_EINVAL;
+  stats_ctx* c = new (std::nothrow) stats_ctx();
+  if (!c) return STATS_ENOMEM;
+  c->p = cfg->p;
+  c->mode = cfg->mode;
+  c->dtypes.assign(cfg->dtypes, cfg->dtypes + cfg->p);
+  for (int32_t dt : c->dtypes)
+    if (dt < I16 || dt > F64) {
+      delete c;
+      return STATS_EINVAL;
+    }
+  c->ident.assign(cfg->p, 0);
+  if (cfg->is_identifier)
+    for (int j = 0; j < cfg->p; ++j) c->ident[j] = cfg->is_identifier[j] ? 1 : 0;
+  c->has_bounds = cfg->lo != nullptr;
+  if (c->has_bounds) {
+    c->lo.assign(cfg->lo, cfg->lo + cfg->p);
+    c->hi.assign(cfg->hi, cfg->hi + cfg->p);
+  }
+  c->pa = 0;
+  for (int j = 0; j < c->p; ++j) c->pa += c->ident[j] ? 0 : 1;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return STATS_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->sms < 1) c->sms = 1;
+
+  stats_status s = STATS_OK;
+  if (c->mode == STATS_EXACT) {
+    s = build_plan(c);
+    if (s != STATS_OK) {
+      delete c;
+      return s;
+    }
+    // pipeline stage layout
+    int off = 0;
+    int row_bytes = 0;
+    for (int j = 0; j < c->p; ++j) {
+      const int b = dtype_bytes(c->dtypes[j]);
+      c->xp.dtype[j] = c->dtypes[j];
+      c->xp.col_bytes[j] = b;
+      c->xp.col_off[j] = off;
+      off += ((kExactTile * b + 127) / 128) * 128;
+      row_bytes += b;
+      c->xp.real_shift[j] = c->plan[j].shift;
+      c->xp.real_emax[j] = c->plan[j].emax;
+      c->xp.kbytes[j] = c->plan[j].k;
+      c->xp.is_signed[j] = c->plan[j].is_signed;
+    }
+    c->xp.p = c->p;
+    c->xp.stage_bytes = off;
+    c->stages = 3;
+    if (exact_smem_bytes(3, off) > 226 * 1024) c->stages = 2;
+    if (exact_smem_bytes(c->stages, off) > 226 * 1024) {
+      delete c;
+      return STATS_EINVAL;  // rows too wide for the pipeline
+    }
+    c->xp.stages = c->stages;
+    (void)row_bytes;
+  }
+  // device allocations
+  cudaError_t e = cudaSuccess;
+  const size_t T = static_cast<size_t>(c->p) * (c->p + 1) / 2;
+  if (c->mode == STATS_EXACT) {
+    e = cudaMalloc(&c->d_g, kDigits * kDigits * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_g, 0, kDigits * kDigits * sizeof(long long));
+    // scratch: per-call accumulator, ticket, error word, status word
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_call, kDigits * kDigits * sizeof(unsigned long long) + 256);
+    if (e == cudaSuccess) e = cudaMemset(c->d_call, 0, kDigits * kDigits * sizeof(unsigned long long) + 256);
+    if (e == cudaSuccess) {
+      unsigned int* words = reinterpret_cast<unsigned int*>(c->d_call + kDigits * kDigits);
+      c->d_ticket = words;
+      c->d_err = words + 1;
+      c->d_status = words + 2;
+      c->xp.call_acc = c->d_call;
+      c->xp.ticket = c->d_ticket;
+      c->xp.err = c->d_err;
+      c->xp.acc = c->d_g;
+      c->xp.status = c->d_status;
+    }
+  } else {
+    const size_t nd = 2 * c->p + 2 * T + c->p + 2;
+    e = cudaMalloc(&c->d_fs, nd * sizeof(double) + 256);
+    if (e == cudaSuccess) e = cudaMemset(c->d_fs, 0, nd * sizeof(double) + 256);
+    if (e == cudaSuccess) {
+      c->d_fs_lo = c->d_fs + c->p;
+      c->d_fS = c->d_fs_lo + c->p;
+      c->d_fS_lo = c->d_fS + T;
+      c->d_shift = c->d_fS_lo + T;
+      c->d_fn = reinterpret_cast<long long*>(c->d_shift + c->p);
+      c->d_status = reinterpret_cast<unsigned int*>(c->d_fn + 1);
+    }
+  }
+  c->lay = final_layout(c->p, c->pa);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_out, c->lay.total * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_work, (2 * static_cast<size_t>(c->pa) * c->pa + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, c->lay.total * sizeof(double));
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return e == cudaErrorMemoryAllocation ? STATS_ENOMEM : STATS_ECUDA;
+  }
+  *out = c;
+  return STATS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+stats_status stats_init(stats_ctx** out, const stats_config* cfg) { return create(out, cfg); }
+
+stats_status stats_accumulate(stats_ctx* ctx, const void* const* dcols, int64_t nrows, void* stream) {
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  if (nrows < 0 || (nrows > 0 && !dcols)) return STATS_EINVAL;
+  for (int j = 0; j < ctx->p && nrows > 0; ++j)
+    if (!dcols[j] || (reinterpret_cast<uintptr_t>(dcols[j]) % dtype_bytes(ctx->dtypes[j])) != 0)
+      return STATS_EINVAL;
+  return launch_pass(ctx, dcols, nrows, static_cast<cudaStream_t>(stream));
+}
+
+stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int64_t nrows, int64_t chunk_rows,
+                                   void* stream) {
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  if (nrows < 0 || chunk_rows < 0 || (nrows > 0 && !hcols)) return STATS_EINVAL;
+  for (int j = 0; j < ctx->p && nrows > 0; ++j)
+    if (!hcols[j]) return STATS_EINVAL;
+  if (nrows == 0) return STATS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (chunk_rows == 0) chunk_rows = kDefaultChunkRows;
+  chunk_rows = (chunk_rows + 7) & ~int64_t(7);
+  if (chunk_rows > nrows) chunk_rows = (nrows + 7) & ~int64_t(7);
+  // (re)allocate the two staging buffers
+  if (ctx->stage_rows < chunk_rows) {
+    for (int b = 0; b < 2; ++b) {
+      if (ctx->d_stage[b]) CK(ctx, cudaFree(ctx->d_stage[b]));
+      ctx->d_stage[b] = nullptr;
+    }
+    ctx->stage_off.assign(ctx->p, 0);
+    size_t off = 0;
+    for (int j = 0; j < ctx->p; ++j) {
+      ctx->stage_off[j] = off;
+      off += ((static_cast<size_t>(chunk_rows) * dtype_bytes(ctx->dtypes[j]) + 255) / 256) * 256;
+    }
+    for (int b = 0; b < 2; ++b) {
+      cudaError_t e = cudaMalloc(&ctx->d_stage[b], off);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return STATS_ENOMEM;
+      }
+      CK(ctx, e);
+    }
+    ctx->stage_rows = chunk_rows;
+  }
+  if (!ctx->copy_stream) {
+    CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
+    }
+  }
+  std::vector<const void*> dcols(ctx->p);
+  int64_t chunk = 0;
+  for (int64_t r0 = 0; r0 < nrows; r0 += chunk_rows, ++chunk) {
+    const int b = static_cast<int>(chunk & 1);
+    const int64_t rows = std::min(chunk_rows, nrows - r0);
+    // the pass that last read buffer b must be done before it is overwritten
+    CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
+    for (int j = 0; j < ctx->p; ++j) {
+      const size_t eb = dtype_bytes(ctx->dtypes[j]);
+      char* dst = static_cast<char*>(ctx->d_stage[b]) + ctx->stage_off[j];
+      const char* src = static_cast<const char*>(hcols[j]) + static_cast<size_t>(r0) * eb;
+      CK(ctx, cudaMemcpyAsync(dst, src, static_cast<size_t>(rows) * eb, cudaMemcpyHostToDevice, ctx->copy_stream));
+      dcols[j] = dst;
+    }
+    CK(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    CK(ctx, cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+    s = launch_pass(ctx, dcols.data(), rows, st);
+    if (s != STATS_OK) return s;
+    CK(ctx, cudaEventRecord(ctx->ev_done[b], st));
+  }
+  return STATS_OK;
+}
+
+stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
+  stats_status s = check_sticky(dst);
+  if (s != STATS_OK) return s;
+  if (!src || src->sticky != STATS_OK) return src ? STATS_ESTATE : STATS_EINVAL;
+  if (dst->p != src->p || dst->mode != src->mode || dst->dtypes != src->dtypes || dst->ident != src->ident)
+    return STATS_EINVAL;
+  if (dst->mode == STATS_EXACT) {
+    for (int j = 0; j < dst->p; ++j)
+      if (dst->plan[j].off != src->plan[j].off || dst->plan[j].k != src->plan[j].k ||
+          dst->plan[j].shift != src->plan[j].shift || dst->plan[j].is_signed != src->plan[j].is_signed)
+        return STATS_EINVAL;
+  }
+  if (dst->mode == STATS_FP64_SHIFTED) return STATS_EINVAL;  // shifts of two ctxs generally differ
+  if (src->last) CK(dst, cudaStreamSynchronize(src->last));
+  stats_ctx* srcm = const_cast<stats_ctx*>(src);
+  // carry src's device error bits over
+  unsigned int bits = 0;
+  CK(dst, cudaMemcpy(&bits, srcm->d_status, sizeof(bits), cudaMemcpyDeviceToHost));
+  if (bits) {
+    unsigned int mine = 0;
+    CK(dst, cudaMemcpy(&mine, dst->d_status, sizeof(mine), cudaMemcpyDeviceToHost));
+    mine |= bits;
+    CK(dst, cudaMemcpy(dst->d_status, &mine, sizeof(mine), cudaMemcpyHostToDevice));
+  }
+  cudaStream_t st = dst->last;
+  if (dst->mode == STATS_EXACT) {
+    CK(dst, launch_merge_i64(dst->d_g, src->d_g, kDigits * kDigits, st));
+  } else {
+    const int T = dst->p * (dst->p + 1) / 2;
+    CK(dst, launch_merge_dd(dst->d_fs, dst->d_fs_lo, src->d_fs, src->d_fs_lo, dst->p, st));
+    CK(dst, launch_merge_dd(dst->d_fS, dst->d_fS_lo, src->d_fS, src->d_fS_lo, T, st));
+    CK(dst, launch_merge_i64(dst->d_fn, src->d_fn, 1, st));
+  }
+  return STATS_OK;
+}
+
+stats_status stats_sync(stats_ctx* ctx) {
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  CK(ctx, cudaStreamSynchronize(ctx->last));
+  if (ctx->copy_stream) CK(ctx, cudaStreamSynchronize(ctx->copy_stream));
+  return device_status(ctx);
+}
+
+stats_status stats_reset(stats_ctx* ctx) {
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  // stream-ordered: work already enqueued on the ctx's stream completes first
+  cudaStream_t st = ctx->last;
+  if (ctx->mode == STATS_EXACT) {
+    CK(ctx, cudaMemsetAsync(ctx->d_g, 0, kDigits * kDigits * sizeof(long long), st));
+  } else {
+    const size_t T = static_cast<size_t>(ctx->p) * (ctx->p + 1) / 2;
+    CK(ctx, cudaMemsetAsync(ctx->d_fs, 0, (2 * ctx->p + 2 * T + ctx->p + 2) * sizeof(double), st));
+    ctx->shift_set = false;
+  }
+  CK(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), st));
+  return STATS_OK;
+}
+
+stats_status stats_raw(stats_ctx* ctx, int64_t* n, double* s, double* S_upper, stats_i128* s_exact,
+                       stats_i128* S_exact_upper) {
+  stats_status st = stats_sync(ctx);
+  if (st != STATS_OK) return st;
+  st = run_finalize(ctx, 0, 0);
+  if (st != STATS_OK) return st;
+  const FinalLayout& L = ctx->lay;
+  const double* h = ctx->h_out;
+  const int p = ctx->p;
+  const int T = p * (p + 1) / 2;
+  if (n) memcpy(n, h + L.n, sizeof(int64_t));
+  if (s) memcpy(s, h + L.s, sizeof(double) * p);
+  if (S_upper) memcpy(S_upper, h + L.S, sizeof(double) * T);
+  if (s_exact) memcpy(s_exact, h + L.s_ex, sizeof(stats_i128) * p);
+  if (S_exact_upper) memcpy(S_exact_upper, h + L.S_ex, sizeof(stats_i128) * T);
+  return h[L.flags] != 0.0 ? STATS_EOVERFLOW : STATS_OK;
+}
+
+stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals, double* evecs,
+                            int32_t pca_on) {
+  stats_status st = stats_sync(ctx);
+  if (st != STATS_OK) return st;
+  if (pca_on != 0 && pca_on != 1) return STATS_EINVAL;
+  // the row count decides whether a covariance exists
+  int64_t n = 0;
+  if (ctx->mode == STATS_EXACT) {
+    CK(ctx, cudaMemcpy(&n, ctx->d_g, sizeof(n), cudaMemcpyDeviceToHost));
+  } else {
+    CK(ctx, cudaMemcpy(&n, ctx->d_fn, sizeof(n), cudaMemcpyDeviceToHost));
+  }
+  if (n < 2) return STATS_EINVAL;
+  st = run_finalize(ctx, (evals || evecs) ? 1 : 0, pca_on);
+  if (st != STATS_OK) return st;
+  const FinalLayout& L = ctx->lay;
+  const double* h = ctx->h_out;
+  const size_t pa = ctx->pa;
+  if (mean) memcpy(mean, h + L.mean, sizeof(double) * pa);
+  if (cov) memcpy(cov, h + L.cov, sizeof(double) * pa * pa);
+  if (corr) memcpy(corr, h + L.corr, sizeof(double) * pa * pa);
+  if (evals) memcpy(evals, h + L.evals, sizeof(double) * pa);
+  if (evecs) memcpy(evecs, h + L.evecs, sizeof(double) * pa * pa);
+  return STATS_OK;
+}
+
+// Checkpoint image: magic, version, p, mode, has_bounds, dtypes, ident, lo, hi,
+// shift_set, then the accumulator words.
+stats_status stats_export(stats_ctx* ctx, void* buf, size_t* len) {
+  if (!len) return STATS_EINVAL;
+  stats_status st = stats_sync(ctx);
+  if (st != STATS_OK) return st;
+  const int p = ctx->p;
+  const size_t T = static_cast<size_t>(p) * (p + 1) / 2;
+  const size_t acc_bytes = ctx->mode == STATS_EXACT ? kDigits * kDigits * sizeof(long long)
+                                                    : (2 * p + 2 * T + p + 1) * sizeof(double);
+  const size_t need = 8 + 4 * 4 + p * 4 + p + 2 * p * 8 + 4 + acc_bytes;
+  if (!buf || *len < need) {
+    *len = need;
+    return buf ? STATS_EINVAL : STATS_OK;
+  }
+  char* w = static_cast<char*>(buf);
+  auto put = [&](const void* src, size_t n) {
+    memcpy(w, src, n);
+    w += n;
+  };
+  const int32_t version = 1, mode = ctx->mode, hb = ctx->has_bounds ? 1 : 0, ss = ctx->shift_set ? 1 : 0;
+  put(&kMagic, 8);
+  put(&version, 4);
+  put(&p, 4);
+  put(&mode, 4);
+  put(&hb, 4);
+  put(ctx->dtypes.data(), 4 * p);
+  put(ctx->ident.data(), p);
+  std::vector<double> lo(p, 0.0), hi(p, 0.0);
+  if (ctx->has_bounds) {
+    lo = ctx->lo;
+    hi = ctx->hi;
+  }
+  put(lo.data(), 8 * p);
+  put(hi.data(), 8 * p);
+  put(&ss, 4);
+  if (ctx->mode == STATS_EXACT) {
+    CK(ctx, cudaMemcpy(w, ctx->d_g, acc_bytes, cudaMemcpyDeviceToHost));
+  } else {
+    CK(ctx, cudaMemcpy(w, ctx->d_fs, acc_bytes, cudaMemcpyDeviceToHost));
+  }
+  *len = need;
+  return STATS_OK;
+}
+
+stats_status stats_import(stats_ctx** out, const void* buf, size_t len) {
+  if (!out || !buf || len < 28) return STATS_EINVAL;
+  const char* r = static_cast<const char*>(buf);
+  const char* end = r + len;
+  auto get = [&](void* dst, size_t n) -> bool {
+    if (r + n > end) return false;
+    memcpy(dst, r, n);
+    r += n;
+    return true;
+  };
+  uint64_t magic = 0;
+  int32_t version = 0, p = 0, mode = 0, hb = 0, ss = 0;
+  if (!get(&magic, 8) || magic != kMagic || !get(&version, 4) || version != 1 || !get(&p, 4) || !get(&mode, 4) ||
+      !get(&hb, 4))
+    return STATS_EINVAL;
+  if (p < 1 || p > STATS_MAX_P) return STATS_EINVAL;
+  std::vector<int32_t> dt(p);
+  std::vector<uint8_t> id(p);
+  std::vector<double> lo(p), hi(p);
+  if (!get(dt.data(), 4 * p) || !get(id.data(), p) || !get(lo.data(), 8 * p) || !get(hi.data(), 8 * p) ||
+      !get(&ss, 4))
+    return STATS_EINVAL;
+  stats_config cfg{p, dt.data(), id.data(), hb ? lo.data() : nullptr, hb ? hi.data() : nullptr, mode};
+  stats_ctx* c = nullptr;
+  stats_status st = stats_init(&c, &cfg);
+  if (st != STATS_OK) return st;
+  const size_t T = static_cast<size_t>(p) * (p + 1) / 2;
+  const size_t acc_bytes = mode == STATS_EXACT ? kDigits * kDigits * sizeof(long long)
+                                               : (2 * p + 2 * T + p + 1) * sizeof(double);
+  if (r + acc_bytes > end) {
+    stats_destroy(c);
+    return STATS_EINVAL;
+  }
+  cudaError_t e = cudaMemcpy(mode == STATS_EXACT ? static_cast<void*>(c->d_g) : static_cast<void*>(c->d_fs), r,
+                             acc_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    stats_destroy(c);
+    return STATS_ECUDA;
+  }
+  c->shift_set = ss != 0;
+  *out = c;
+  return STATS_OK;
+}
+
+void stats_destroy(stats_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->last) cudaStreamSynchronize(ctx->last);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+  free_ctx(ctx);
+}
+
+const char* stats_strerror(stats_status st) {
+  switch (st) {
+    case STATS_OK: return "ok";
+    case STATS_EINVAL: return "invalid argument or configuration";
+    case STATS_ENOMEM: return "out of memory";
+    case STATS_ECUDA: return "CUDA runtime error";
+    case STATS_EOVERFLOW: return "exact result does not fit its output type";
+    case STATS_ETIMEOUT: return "a bounded device-side wait expired";
+    case STATS_ESTATE: return "context failed earlier or call out of order";
+    case STATS_ERANGE: return "a value lay outside the digit field of its declared range";
+    default: return "unknown status";
+  }
+}
+
+int32_t stats_num_analysis_columns(const stats_ctx* ctx) { return ctx ? ctx->pa : -1; }
+
+stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks) {
+  if (!ctx || blocks < 0) return STATS_EINVAL;
+  ctx->grid = blocks;
+  return STATS_OK;
+}
+
+int32_t stats_table1_row_bytes(int32_t layout) {
+  return layout == STATS_T1_L32 ? 60 : layout == STATS_T1_L16 ? 44 : 0;
+}
+
+stats_status stats_table1_config(int32_t layout, int64_t max_rows, int32_t* dtypes, uint8_t* is_identifier,
+                                 double* lo, double* hi) {
+  if (layout != STATS_T1_L32 && layout != STATS_T1_L16) return STATS_EINVAL;
+  if (max_rows < 1 || max_rows >= (int64_t(1) << 40)) return STATS_EINVAL;
+  static const int32_t l32[12] = {I64, I32, I32, I32, I32, I32, I32, I32, F64, I32, F64, I32};
+  static const int32_t l16[12] = {I64, I16, I16, I16, I16, I32, I16, I16, F64, I16, F64, I16};
+  // value ranges produced by the Table 1 formulas: |cotC| <= |cot 3| = 7.0153, J <= |tan 11| = 225.951
+  const double rlo[12] = {1, 3, 1, 1, 0, 0, 0, 0, -7.1, 0, 0, 0};
+  const double rhi[12] = {static_cast<double>(max_rows), 8, 10, 100, 255, 65535, 100, 100, 7.1, 65535, 226, 100};
+  for (int j = 0; j < 12; ++j) {
+    if (dtypes) dtypes[j] = layout == STATS_T1_L32 ? l32[j] : l16[j];
+    if (is_identifier) is_identifier[j] = j == 0 ? 1 : 0;
+    if (lo) lo[j] = rlo[j];
+    if (hi) hi[j] = rhi[j];
+  }
+  return STATS_OK;
+}
+
+stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32_t layout, void* const* dcols,
+                              void* stream) {
+  if (layout != STATS_T1_L32 && layout != STATS_T1_L16) return STATS_EINVAL;
+  if (nrows < 0 || (nrows > 0 && !dcols)) return STATS_EINVAL;
+  if (nrows == 0) return STATS_OK;
+  for (int j = 0; j < 12; ++j)
+    if (!dcols[j] || !aligned16(dcols[j])) return STATS_EINVAL;
+  cudaError_t e = launch_gen_table1(seed, row0, nrows, layout, dcols, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? STATS_OK : STATS_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,453 @@
+// k_finalize.cu -- from the sufficient statistics (n, s, S) to mean,
+// covariance, correlation and the PCA eigenpairs, in one thread block on the
+// device (arxiv 2604.23826: "Data Representation and Sufficient Statistics" --
+// mean, covariance and correlation from the aggregated matrices only;
+// "Numerical Considerations" -- cancellation between X^T X and N mu mu^T, and the
+// identifier dropped from the analysis; "Principal Component Analysis Results"
+// -- eigenpairs of the p x p matrix).
+//
+// STATS_EXACT: the digit Gram G is recombined into exact integers
+//   r_j = sum_a 256^a G[0][(j,a)],  R_jk = sum_{a,b} 256^(a+b) G[(j,a)][(k,b)]
+// (values scaled by 2^-shift for real columns), in 256-bit two's complement
+// arithmetic, and centred exactly: C_jk = n R_jk - r_j r_k, so no cancellation
+// can occur; cov_jk = C_jk 2^-(shift_j + shift_k) / (n (n - 1)) is then rounded.
+// STATS_FP64: the paper's raw-moment formula (S_jk - s_j s_k / n) / (n - 1) in FP64.
+// Eigenpairs: cyclic Jacobi with the parallel round-robin ordering (Brent & Luk):
+// each round applies n/2 rotations on disjoint index pairs at once.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ss {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------- 256-bit integers -------------------------------
+struct i256 {
+  uint64_t w[4];  // two's complement, w[0] least significant
+};
+
+__device__ __forceinline__ i256 i256_from(int64_t v) {
+  const uint64_t ext = v < 0 ? ~0ull : 0ull;
+  return i256{{static_cast<uint64_t>(v), ext, ext, ext}};
+}
+__device__ __forceinline__ bool i256_neg(const i256& a) { return static_cast<int64_t>(a.w[3]) < 0; }
+__device__ __forceinline__ bool i256_zero(const i256& a) { return !(a.w[0] | a.w[1] | a.w[2] | a.w[3]); }
+
+__device__ __forceinline__ i256 i256_add(const i256& a, const i256& b) {
+  i256 r;
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t s = a.w[i] + b.w[i];
+    const uint64_t c1 = s < a.w[i];
+    r.w[i] = s + c;
+    const uint64_t c2 = r.w[i] < s;
+    c = c1 | c2;
+  }
+  return r;
+}
+__device__ __forceinline__ i256 i256_negate(const i256& a) {
+  i256 r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.w[i] = ~a.w[i];
+  return i256_add(r, i256_from(1));
+}
+__device__ __forceinline__ i256 i256_sub(const i256& a, const i256& b) { return i256_add(a, i256_negate(b)); }
+__device__ __forceinline__ i256 i256_abs(const i256& a) { return i256_neg(a) ? i256_negate(a) : a; }
+
+// a << bits, 0 <= bits < 256
+__device__ __forceinline__ i256 i256_shl(const i256& a, int bits) {
+  i256 r{{0, 0, 0, 0}};
+  const int lw = bits >> 6, b = bits & 63;
+  for (int i = 3; i >= 0; --i) {
+    const int src = i - lw;
+    if (src < 0) continue;
+    uint64_t v = a.w[src] << b;
+    if (b && src > 0) v |= a.w[src - 1] >> (64 - b);
+    r.w[i] = v;
+  }
+  return r;
+}
+
+// |a| * |b| modulo 2^256, unsigned limbs
+__device__ __forceinline__ i256 u256_mul(const i256& a, const i256& b) {
+  i256 r{{0, 0, 0, 0}};
+  for (int i = 0; i < 4; ++i) {
+    uint64_t carry = 0;
+    for (int j = 0; i + j < 4; ++j) {
+      const uint64_t lo = a.w[i] * b.w[j];
+      const uint64_t hi = __umul64hi(a.w[i], b.w[j]);
+      uint64_t s = r.w[i + j] + lo;
+      uint64_t c = s < lo;
+      s += carry;
+      c += s < carry;
+      r.w[i + j] = s;
+      carry = hi + c;
+    }
+  }
+  return r;
+}
+__device__ __forceinline__ i256 i256_mul(const i256& a, const i256& b) {
+  const bool neg = i256_neg(a) != i256_neg(b);
+  const i256 m = u256_mul(i256_abs(a), i256_abs(b));
+  return neg ? i256_negate(m) : m;
+}
+
+// Correctly rounded conversion to double (round to nearest even): the top 64
+// significant bits with a sticky bit for everything below them.
+__device__ double i256_to_double(const i256& a) {
+  if (i256_zero(a)) return 0.0;
+  const bool neg = i256_neg(a);
+  const i256 m = i256_abs(a);
+  int top = 3;
+  while (top > 0 && m.w[top] == 0) --top;
+  const int lz = __clzll(static_cast<long long>(m.w[top]));
+  const int msb = top * 64 + 63 - lz;  // index of the highest set bit
+  double d;
+  if (msb < 64) {
+    d = __ull2double_rn(m.w[0]);
+  } else {
+    const int sh = msb - 63;  // drop sh low bits
+    const i256 t = i256{{0, 0, 0, 0}};
+    (void)t;
+    const int lw = sh >> 6, b = sh & 63;
+    uint64_t hi64 = m.w[lw] >> b;
+    if (b && lw + 1 < 4) hi64 |= m.w[lw + 1] << (64 - b);
+    uint64_t sticky = 0;
+    for (int i = 0; i < lw; ++i) sticky |= m.w[i];
+    if (b) sticky |= m.w[lw] & ((1ull << b) - 1);
+    d = ldexp(__ull2double_rn(hi64 | (sticky ? 1ull : 0ull)), sh);
+  }
+  return neg ? -d : d;
+}
+
+__device__ bool i256_fits_i128(const i256& a, int64_t& lo, int64_t& hi) {
+  lo = static_cast<int64_t>(a.w[0]);
+  hi = static_cast<int64_t>(a.w[1]);
+  const uint64_t ext = hi < 0 ? ~0ull : 0ull;
+  return a.w[2] == ext && a.w[3] == ext;
+}
+
+// ------------------------------- Jacobi (one block) -------------------------------
+// A (m x m padded, row-major, lda = pa) symmetric in global scratch; V likewise.
+__device__ void jacobi_block(double* A, double* V, int pa, double* evals, double* evecs, double* flags) {
+  __shared__ double s_c[kThreads], s_s[kThreads];
+  __shared__ int s_p[kThreads], s_q[kThreads];
+  __shared__ double s_red[kThreads];
+  __shared__ int s_done;
+  const int tid = threadIdx.x;
+  const int m = pa + (pa & 1);  // even number of indices; index pa is a dummy when pa is odd
+  for (int i = tid; i < pa * pa; i += blockDim.x) V[i] = (i / pa == i % pa) ? 1.0 : 0.0;
+  __syncthreads();
+  // Frobenius norm for the stopping test
+  double loc = 0.0;
+  for (int i = tid; i < pa * pa; i += blockDim.x) loc += A[i] * A[i];
+  s_red[tid] = loc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) s_red[tid] += s_red[tid + w];
+    __syncthreads();
+  }
+  const double fro2 = s_red[0];
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    loc = 0.0;
+    for (int i = tid; i < pa * pa; i += blockDim.x)
+      if (i / pa != i % pa) loc += A[i] * A[i];
+    s_red[tid] = loc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (tid < w) s_red[tid] += s_red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) s_done = (s_red[0] == 0.0 || s_red[0] <= 1e-34 * fro2) ? 1 : 0;
+    __syncthreads();
+    if (s_done) break;
+    for (int round = 0; round < m - 1; ++round) {
+      // pairs of this round: (m-1, round) and ((round+i) mod (m-1), (round-i) mod (m-1))
+      for (int i = tid; i < m / 2; i += blockDim.x) {
+        int p, q;
+        if (i == 0) {
+          p = round;
+          q = m - 1;
+        } else {
+          p = (round + i) % (m - 1);
+          q = (round - i + (m - 1)) % (m - 1);
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < pa) {
+          const double apq = A[p * pa + q];
+          if (apq != 0.0) {
+            const double theta = (A[q * pa + q] - A[p * pa + p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        s_c[i] = c;
+        s_s[i] = s;
+        s_p[i] = p;
+        s_q[i] = q;
+      }
+      __syncthreads();
+      // rows: (row p, row q) <- (c row p - s row q, s row p + c row q)
+      for (int idx = tid; idx < (m / 2) * pa; idx += blockDim.x) {
+        const int i = idx / pa, k = idx % pa;
+        const int p = s_p[i], q = s_q[i];
+        if (q >= pa || s_s[i] == 0.0) continue;
+        const double c = s_c[i], s = s_s[i];
+        const double apk = A[p * pa + k], aqk = A[q * pa + k];
+        A[p * pa + k] = c * apk - s * aqk;
+        A[q * pa + k] = s * apk + c * aqk;
+      }
+      __syncthreads();
+      // columns of A and V
+      for (int idx = tid; idx < (m / 2) * pa; idx += blockDim.x) {
+        const int i = idx / pa, k = idx % pa;
+        const int p = s_p[i], q = s_q[i];
+        if (q >= pa || s_s[i] == 0.0) continue;
+        const double c = s_c[i], s = s_s[i];
+        const double akp = A[k * pa + p], akq = A[k * pa + q];
+        A[k * pa + p] = c * akp - s * akq;
+        A[k * pa + q] = s * akp + c * akq;
+        const double vkp = V[k * pa + p], vkq = V[k * pa + q];
+        V[k * pa + p] = c * vkp - s * vkq;
+        V[k * pa + q] = s * vkp + c * vkq;
+      }
+      __syncthreads();
+      for (int i = tid; i < m / 2; i += blockDim.x) {
+        const int p = s_p[i], q = s_q[i];
+        if (q < pa && s_s[i] != 0.0) {
+          A[p * pa + q] = 0.0;
+          A[q * pa + p] = 0.0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // order descending; sign: largest-magnitude component positive
+  __shared__ int s_order[256];
+  if (tid == 0) {
+    for (int i = 0; i < pa; ++i) s_order[i] = i;
+    for (int i = 0; i < pa; ++i) {
+      int best = i;
+      for (int j = i + 1; j < pa; ++j)
+        if (A[s_order[j] * pa + s_order[j]] > A[s_order[best] * pa + s_order[best]]) best = j;
+      const int t = s_order[i];
+      s_order[i] = s_order[best];
+      s_order[best] = t;
+    }
+    flags[2] = sweep;
+  }
+  __syncthreads();
+  for (int k = tid; k < pa; k += blockDim.x) {
+    const int col = s_order[k];
+    evals[k] = A[col * pa + col];
+    int imax = 0;
+    for (int i = 1; i < pa; ++i)
+      if (fabs(V[i * pa + col]) > fabs(V[imax * pa + col])) imax = i;
+    const double sg = V[imax * pa + col] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < pa; ++i) evecs[k * pa + i] = sg * V[i * pa + col];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 1) finalize_kernel(const __grid_constant__ FinalParams P) {
+  __shared__ long long G[kDigits * kDigits];
+  __shared__ int s_amap[256];  // analysis column index -> table column
+  __shared__ int s_pa;
+  __shared__ int s_zero;
+  __shared__ int s_over;
+  const int tid = threadIdx.x;
+  const int p = P.p;
+  if (tid == 0) {
+    int pa = 0;
+    for (int j = 0; j < p; ++j)
+      if (!P.col[j].is_ident) s_amap[pa++] = j;
+    s_pa = pa;
+    s_zero = 0;
+    s_over = 0;
+  }
+  const FinalLayout L = final_layout(p, 0);  // offsets of n, s, S and exact blocks do not depend on pa
+  __syncthreads();
+  const int pa = s_pa;
+  const FinalLayout LA = final_layout(p, pa);
+  double* out = P.out;
+  double* flags = out + LA.flags;
+  double* cov = out + LA.cov;
+  double* corr = out + LA.corr;
+  const int T = p * (p + 1) / 2;
+  double n_d = 0.0;
+
+  if (P.mode == 0) {
+    // ------------------------------- STATS_EXACT -------------------------------
+    for (int i = tid; i < kDigits * kDigits; i += blockDim.x) {
+      const int r = i / kDigits, c = i % kDigits;
+      G[i] = (r <= c) ? P.g[r * kDigits + c] : P.g[c * kDigits + r];
+    }
+    __syncthreads();
+    const long long n = G[0];
+    n_d = static_cast<double>(n);
+    if (tid == 0) reinterpret_cast<long long*>(out)[L.n] = n;
+    // exact column sums r_j (scaled by 2^-shift_j)
+    for (int j = tid; j < p; j += blockDim.x) {
+      const FinalPlanCol cj = P.col[j];
+      i256 r = i256_from(0);
+      for (int a = 0; a < cj.k; ++a) r = i256_add(r, i256_shl(i256_from(G[cj.off + a]), 8 * a));
+      out[L.s + j] = ldexp(i256_to_double(r), -cj.shift);
+      int64_t lo = 0, hi = 0;
+      if (!cj.is_real) {
+        if (!i256_fits_i128(r, lo, hi)) atomicOr(&s_over, 1);
+      } else {
+        lo = hi = 0;
+      }
+      reinterpret_cast<int64_t*>(out)[L.s_ex + 2 * j] = lo;
+      reinterpret_cast<int64_t*>(out)[L.s_ex + 2 * j + 1] = hi;
+    }
+    // exact cross products R_jk and, for analysis pairs, the exact centred numerator
+    const i256 nn = i256_from(n);
+    for (int t = tid; t < T; t += blockDim.x) {
+      int j = 0, rem = t;
+      while (rem >= p - j) {
+        rem -= p - j;
+        ++j;
+      }
+      const int k = j + rem;
+      const FinalPlanCol cj = P.col[j], ck = P.col[k];
+      i256 R = i256_from(0);
+      for (int a = 0; a < cj.k; ++a)
+        for (int b = 0; b < ck.k; ++b)
+          R = i256_add(R, i256_shl(i256_from(G[(cj.off + a) * kDigits + ck.off + b]), 8 * (a + b)));
+      out[L.S + t] = ldexp(i256_to_double(R), -(cj.shift + ck.shift));
+      int64_t lo = 0, hi = 0;
+      if (!cj.is_real && !ck.is_real) {
+        if (!i256_fits_i128(R, lo, hi)) atomicOr(&s_over, 1);
+      }
+      reinterpret_cast<int64_t*>(out)[L.S_ex + 2 * t] = lo;
+      reinterpret_cast<int64_t*>(out)[L.S_ex + 2 * t + 1] = hi;
+      if (pa > 0 && !cj.is_ident && !ck.is_ident && n >= 2) {
+        i256 rj = i256_from(0), rk = i256_from(0);
+        for (int a = 0; a < cj.k; ++a) rj = i256_add(rj, i256_shl(i256_from(G[cj.off + a]), 8 * a));
+        for (int b = 0; b < ck.k; ++b) rk = i256_add(rk, i256_shl(i256_from(G[ck.off + b]), 8 * b));
+        const i256 C = i256_sub(i256_mul(nn, R), i256_mul(rj, rk));
+        const i256 den = i256_mul(nn, i256_from(n - 1));
+        const double v = ldexp(i256_to_double(C) / i256_to_double(den), -(cj.shift + ck.shift));
+        int aj = 0, ak = 0;
+        for (int q = 0; q < pa; ++q) {
+          if (s_amap[q] == j) aj = q;
+          if (s_amap[q] == k) ak = q;
+        }
+        cov[aj * pa + ak] = v;
+        cov[ak * pa + aj] = v;
+      }
+    }
+    __syncthreads();
+    for (int a = tid; a < pa; a += blockDim.x) {
+      const int j = s_amap[a];
+      out[LA.mean + a] = out[L.s + j] / n_d;
+      if (out[LA.cov + a * pa + a] == 0.0) atomicAdd(&s_zero, 1);
+    }
+  } else {
+    // ------------------------------- FP64 modes -------------------------------
+    const long long n = *P.fn;
+    n_d = static_cast<double>(n);
+    if (tid == 0) reinterpret_cast<long long*>(out)[L.n] = n;
+    // raw sums (shifted sums mapped back: s = s' + n c, S = S' + c s'^T + s' c^T + n c c^T)
+    for (int j = tid; j < p; j += blockDim.x) {
+      double v = P.fs[j] + P.fs_lo[j];
+      if (P.shift) v = fma(n_d, P.shift[j], v);
+      out[L.s + j] = v;
+      reinterpret_cast<int64_t*>(out)[L.s_ex + 2 * j] = 0;
+      reinterpret_cast<int64_t*>(out)[L.s_ex + 2 * j + 1] = 0;
+    }
+    for (int t = tid; t < T; t += blockDim.x) {
+      int j = 0, rem = t;
+      while (rem >= p - j) {
+        rem -= p - j;
+        ++j;
+      }
+      const int k = j + rem;
+      double v = P.fS[t] + P.fS_lo[t];
+      const double sj = P.fs[j] + P.fs_lo[j], sk = P.fs[k] + P.fs_lo[k];
+      if (P.shift) {
+        const double cj = P.shift[j], ck = P.shift[k];
+        v += cj * sk + sj * ck + n_d * cj * ck;
+      }
+      out[L.S + t] = v;
+      reinterpret_cast<int64_t*>(out)[L.S_ex + 2 * t] = 0;
+      reinterpret_cast<int64_t*>(out)[L.S_ex + 2 * t + 1] = 0;
+      if (!P.col[j].is_ident && !P.col[k].is_ident && n >= 2) {
+        // the paper's raw-moment formula on the (shifted) sums, in FP64
+        const double Sjk = P.fS[t] + P.fS_lo[t];
+        const double c = (Sjk - sj * sk / n_d) / (n_d - 1.0);
+        int aj = 0, ak = 0;
+        for (int q = 0; q < pa; ++q) {
+          if (s_amap[q] == j) aj = q;
+          if (s_amap[q] == k) ak = q;
+        }
+        cov[aj * pa + ak] = c;
+        cov[ak * pa + aj] = c;
+      }
+    }
+    __syncthreads();
+    for (int a = tid; a < pa; a += blockDim.x) {
+      const int j = s_amap[a];
+      out[LA.mean + a] = out[L.s + j] / n_d;
+      if (!(out[LA.cov + a * pa + a] > 0.0)) atomicAdd(&s_zero, 1);
+    }
+  }
+  __syncthreads();
+  // correlation: cov_jk / (sqrt(cov_jj) sqrt(cov_kk)); NaN where a variance is not positive
+  for (int i = tid; i < pa * pa; i += blockDim.x) {
+    const int a = i / pa, b = i % pa;
+    const double va = cov[a * pa + a], vb = cov[b * pa + b];
+    double r;
+    if (!(va > 0.0) || !(vb > 0.0))
+      r = __longlong_as_double(0x7ff8000000000000ll);
+    else if (a == b)
+      r = 1.0;
+    else
+      r = cov[i] / (sqrt(va) * sqrt(vb));
+    corr[i] = r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    flags[0] = s_over ? 1.0 : 0.0;
+    flags[1] = s_zero;
+    flags[2] = 0.0;
+    flags[3] = 0.0;
+  }
+  __syncthreads();
+  const bool pca_ok = P.want_pca && pa > 0 && n_d >= 2.0 && !(P.pca_on == 1 && s_zero > 0);
+  if (pca_ok) {
+    double* A = P.work;
+    double* V = P.work + static_cast<size_t>(pa) * pa;
+    const double* src = P.pca_on ? corr : cov;
+    for (int i = tid; i < pa * pa; i += blockDim.x) A[i] = src[i];
+    __syncthreads();
+    jacobi_block(A, V, pa, out + LA.evals, out + LA.evecs, flags);
+    if (tid == 0) flags[3] = 1.0;
+  } else {
+    for (int i = tid; i < pa; i += blockDim.x) out[LA.evals + i] = __longlong_as_double(0x7ff8000000000000ll);
+    for (int i = tid; i < pa * pa; i += blockDim.x) out[LA.evecs + i] = __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream) {
+  finalize_kernel<<<1, kThreads, 0, stream>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -1,0 +1,147 @@
+// kernels.h -- host-side launch interface between the C-ABI layer (api.cu) and
+// the kernel translation units.  Internal to libsuffstats.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ss {
+
+// Status bits written by kernels into a device status word; the host maps them
+// to stats_status codes at the next synchronising call.
+enum : uint32_t {
+  DEV_ERANGE = 1u,    // a value lay outside the digit field of its declared range
+  DEV_ETIMEOUT = 2u,  // a bounded wait (mbarrier) expired
+  DEV_EOVERFLOW = 4u  // an exact result does not fit its output type
+};
+
+constexpr int kMaxCols = 16;     // columns of the EXACT pass
+constexpr int kDigits = 32;      // digit slots of the EXACT pass (ones column included)
+constexpr int kDigitPairs = kDigits / 2;
+
+enum Dtype : int32_t { I16 = 0, I32 = 1, I64 = 2, F32 = 3, F64 = 4 };
+
+inline int dtype_bytes(int32_t dt) { return dt == I16 ? 2 : (dt == I32 || dt == F32) ? 4 : 8; }
+
+// Which converter the EXACT pass uses for a row.
+enum ExactConv : int32_t { CONV_GENERIC = 0, CONV_T1_L32 = 1, CONV_T1_L16 = 2 };
+
+// Parameters of one launch of the EXACT pass (passed by value as a kernel parameter).
+struct ExactParams {
+  const void* cols[kMaxCols];  // device column pointers, element 0 = first row of the call
+  int32_t dtype[kMaxCols];
+  int32_t col_off[kMaxCols];   // byte offset of each column inside a pipeline stage
+  int32_t col_bytes[kMaxCols];
+  int32_t real_shift[kMaxCols];  // real columns: q = RN(x * 2^shift)
+  int32_t real_emax[kMaxCols];   // real columns: largest allowed biased exponent field
+  int32_t kbytes[kMaxCols];      // digit bytes of the column's field
+  int32_t is_signed[kMaxCols];   // field is two's complement (top byte signed)
+  // Generic plan, per digit pair q: source column of the low / high digit
+  // (-1 = the ones column, -2 = zero padding), its byte index, and whether it is
+  // the signed top byte of its field.
+  int8_t pc0[kDigitPairs], pb0[kDigitPairs], ps0[kDigitPairs];
+  int8_t pc1[kDigitPairs], pb1[kDigitPairs], ps1[kDigitPairs];
+  int32_t p;
+  int32_t direct;       // 1: some column is not 16-byte aligned -- consumers read global memory directly
+  int32_t stages;       // pipeline depth (2 or 3)
+  int32_t stage_bytes;  // bytes of one stage (multiple of 128)
+  int64_t nrows;        // rows of this call
+  int64_t nmain;        // rows moved by bulk copies (nrows rounded down to a multiple of 8)
+  unsigned long long* call_acc;  // scratch: kDigits*kDigits int64, zero between calls
+  unsigned int* ticket;          // scratch: block counter, zero between calls
+  unsigned int* err;             // scratch: error bits of this call, zero between calls
+  long long* acc;                // ctx accumulator: kDigits*kDigits int64 (entries r <= c valid)
+  unsigned int* status;          // ctx sticky device status bits
+};
+
+// Rows of one pipeline stage of the EXACT pass.
+constexpr int kExactWarps = 15;                 // consumer warps; +1 producer warp
+constexpr int kExactThreads = (kExactWarps + 1) * 32;
+constexpr int kExactTile = kExactWarps * 64;    // 960 rows per stage
+size_t exact_smem_bytes(int stages, int stage_bytes);
+cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream);
+int exact_max_active_blocks(int conv, int stages, int stage_bytes);
+
+// ---------------------------------------------------------------------------
+// FP64 CUDA-core passes (raw or shifted), fixed-order merge of block slots.
+// ---------------------------------------------------------------------------
+struct Fp64Params {
+  const void* cols[256];
+  int32_t dtype[256];
+  int32_t p;
+  int64_t nrows;
+  const double* shift;  // p values or nullptr (raw moments)
+  double* slots;        // scratch: grid * (T(p) + p) doubles
+  double* acc_s;        // ctx: p doubles (column sums, shifted when shift != nullptr)
+  double* acc_S;        // ctx: T(p) doubles, packed upper
+  double* acc_s_lo;     // ctx: p low parts (double-double)
+  double* acc_S_lo;     // ctx: T(p) low parts
+  long long* acc_n;     // ctx: row count
+};
+cudaError_t launch_fp64(const Fp64Params& P, int grid, cudaStream_t stream);
+size_t fp64_slot_doubles(int grid);  // slots + ticket word, zeroed once at allocation
+cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, double* shift,
+                             cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Finalize (one block): recombination, exact centering, cov / corr, Jacobi.
+// ---------------------------------------------------------------------------
+struct FinalPlanCol {
+  int32_t off;      // first digit slot of the column
+  int32_t k;        // digit bytes
+  int32_t shift;    // real columns: fixed-point shift (value = q * 2^-shift); 0 for integers
+  int32_t is_real;
+  int32_t is_ident;
+};
+struct FinalParams {
+  int32_t p;
+  int32_t mode;      // stats_mode
+  int32_t pca_on;    // 0 cov, 1 corr
+  int32_t want_pca;
+  FinalPlanCol col[256];
+  const long long* g;          // EXACT: digit gram kDigits x kDigits
+  const double* fs;            // FP64: sums (hi), p
+  const double* fs_lo;
+  const double* fS;            // FP64: packed upper (hi)
+  const double* fS_lo;
+  const long long* fn;         // FP64: count
+  const double* shift;         // FP64 shifted: shift vector or nullptr
+  double* out;                 // device result buffer (layout: final_layout())
+  double* work;                // device scratch: 2 * pa * pa doubles
+};
+// Offsets (in doubles) of the finalize result buffer.
+struct FinalLayout {
+  int64_t n, s, S, s_ex, S_ex, mean, cov, corr, evals, evecs, flags, total;
+};
+__host__ __device__ inline FinalLayout final_layout(int p, int pa) {
+  FinalLayout L;
+  const int64_t T = static_cast<int64_t>(p) * (p + 1) / 2;
+  L.n = 0;
+  L.s = 1;
+  L.S = L.s + p;
+  L.s_ex = L.S + T;            // p int128 values as (lo, hi) int64 pairs
+  L.S_ex = L.s_ex + 2 * p;     // T int128 values
+  L.mean = L.S_ex + 2 * T;
+  L.cov = L.mean + pa;
+  L.corr = L.cov + static_cast<int64_t>(pa) * pa;
+  L.evals = L.corr + static_cast<int64_t>(pa) * pa;
+  L.evecs = L.evals + pa;
+  L.flags = L.evecs + static_cast<int64_t>(pa) * pa;
+  L.total = L.flags + 8;
+  return L;
+}
+// flags: [0] an exact integer entry did not fit 128 bits, [1] zero-variance columns,
+//        [2] Jacobi sweeps, [3] eigenpairs computed (1) or not (0)
+cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Table 1 generator and misc.
+// ---------------------------------------------------------------------------
+cudaError_t t1_upload_lut();  // builds the lookup tables with libm on the host, once per device
+cudaError_t launch_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int layout, void* const* cols,
+                              cudaStream_t stream);
+cudaError_t launch_merge_i64(long long* dst, const long long* src, int count, cudaStream_t stream);
+cudaError_t launch_merge_dd(double* dst_hi, double* dst_lo, const double* src_hi, const double* src_lo, int count,
+                            cudaStream_t stream);
+
+}  // namespace ss
