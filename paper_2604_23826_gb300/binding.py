@@ -342,3 +342,4 @@ def gen_table1(seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0,
         cols = alloc_table1(nrows, layout)
     stats_gen_table1(seed, row0, nrows, layout, cols, stream)
     return cols
+

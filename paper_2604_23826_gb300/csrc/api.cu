@@ -392,7 +392,7 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
       c->xp.dtype[j] = c->dtypes[j];
       c->xp.col_bytes[j] = b;
       c->xp.col_off[j] = off;
-      off += ((kExactTile * b + 127) / 128) * 128;
+      off += stage_col_bytes(b);
       row_bytes += b;
       c->xp.real_shift[j] = c->plan[j].shift;
       c->xp.real_emax[j] = c->plan[j].emax;
@@ -791,3 +791,4 @@ stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32
 }
 
 }  // extern "C"
+

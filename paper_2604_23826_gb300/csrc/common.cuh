@@ -141,27 +141,36 @@ __device__ __forceinline__ uint32_t digits2(uint32_t packed_bytes, uint32_t bias
 }
 
 // ---------------------------------------------------------------------------
-// RN(x * 2^sh) as a two's complement int64, with integer operations only (no
-// FP64 pipe).  Valid when |x| * 2^sh < 2^62.  Round half to even.
+// Fixed point of a double: q = round(x * 2^sh) as a two's complement int64,
+// ties rounded up in magnitude, with 32-bit integer operations only (no FP64
+// pipe, no branches).  x = m * 2^(E - 1075) with the 53-bit significand m, so
+// 2 * |q| + 1 >= T = floor(m * 2^(E - 1075 + sh + 1)) and |q| = (T + 1) >> 1.
+// Valid when |x| * 2^sh < 2^62 and the left shift E - 1075 + sh + 1 < 32
+// (both hold for every value that passes the field check, |x| < 2^e with
+// sh = P - e, P <= 55); values outside are flagged by that check.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t fixed_rn(double x, int sh) {
-  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x));
-  const int e = static_cast<int>((u >> 52) & 0x7FF);
-  const uint64_t frac = u & 0x000FFFFFFFFFFFFFull;
-  const uint64_t m = e ? (frac | (1ull << 52)) : frac;  // x = m * 2^(max(e,1) - 1075)
-  const int r = 1075 - sh - (e ? e : 1);                // right shift to reach integer units
-  uint64_t q;
-  if (r <= 0) {
-    q = m << (-r);
-  } else if (r >= 64) {
-    q = 0;  // |x * 2^sh| < 2^53 / 2^64: rounds to 0
-  } else {
-    q = m >> r;
-    const uint64_t rem = m & ((1ull << r) - 1);
-    const uint64_t half = 1ull << (r - 1);
-    q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+template <bool Signed>
+__device__ __forceinline__ uint64_t fixed_rn(double x, int sh) {
+  const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+  const int e = static_cast<int>((hi >> 20) & 0x7FF);
+  const uint32_t mh = (hi & 0x000FFFFFu) | (e ? 0x00100000u : 0u);
+  const int k = max(e, 1) - 1075 + sh + 1;  // left shift of m that gives T
+  const uint32_t ls = static_cast<uint32_t>(min(max(k, 0), 31));
+  const uint32_t rs = static_cast<uint32_t>(min(max(-k, 0), 63));
+  // T = m << ls >> rs
+  const uint32_t h1 = __funnelshift_l(lo, mh, ls);
+  const uint32_t l1 = lo << ls;
+  const uint32_t l2 = rs < 32 ? __funnelshift_r(l1, h1, rs) : (h1 >> (rs - 32));
+  const uint32_t h2 = rs < 32 ? (h1 >> rs) : 0u;
+  // |q| = (T + 1) >> 1
+  const uint64_t t = ((static_cast<uint64_t>(h2) << 32) | l2) + 1ull;
+  uint64_t q = t >> 1;
+  if (Signed) {
+    const uint64_t neg = static_cast<uint64_t>(-static_cast<int64_t>(hi >> 31));  // 0 or all ones
+    q = (q ^ neg) - neg;
   }
-  return (u >> 63) ? -static_cast<int64_t>(q) : static_cast<int64_t>(q);
+  return q;
 }
 
 // Biased binary exponent field of a double (0 for zero / subnormal).

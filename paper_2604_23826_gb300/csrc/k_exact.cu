@@ -5,7 +5,7 @@
 // Every row becomes a vector w of 32 small integer "digits": the ones column
 // (so that n and s fall out of the same product), then each column's value split
 // into base-256 digits (integers directly; real columns first as a fixed-point
-// integer q = RN(x * 2^shift) of their declared range).  The digit Gram matrix
+// integer q = round(x * 2^shift) of their declared range, ties away from zero).  The digit Gram matrix
 // G = sum_rows w w^T is accumulated on the tensor cores with f16 operands
 // (every digit |d| <= 255 is exact in f16) and FP32 accumulators.  Each product
 // is below 2^16 and a warp flushes its accumulators every 256 of its rows, so
@@ -68,12 +68,36 @@ struct GlobalSrc {
   __device__ __forceinline__ float f32(int j) const { return static_cast<const float*>(P->cols[j])[r]; }
 };
 
+// Stage layout of the Table 1 layouts, known at compile time (the host lays a
+// stage out with the same rule: columns in order, stage_col_bytes() each).
+template <bool L16>
+struct T1Layout {
+  __host__ __device__ static constexpr int bytes(int j) { return (j == 0 || j == 8 || j == 10) ? 8 : (L16 && j != 5) ? 2 : 4; }
+  __host__ __device__ static constexpr int off(int j) {
+    int o = 0;
+    for (int i = 0; i < j; ++i) o += stage_col_bytes(bytes(i));
+    return o;
+  }
+};
+template <bool L16>
+struct SmemT1Src {
+  const uint8_t* base;  // stage base
+  int r;                // row inside the stage
+  __device__ __forceinline__ int32_t i32(int j) const { return *reinterpret_cast<const int32_t*>(base + T1Layout<L16>::off(j) + r * 4); }
+  __device__ __forceinline__ int32_t i16(int j) const { return *reinterpret_cast<const int16_t*>(base + T1Layout<L16>::off(j) + r * 2); }
+  __device__ __forceinline__ int64_t i64(int j) const { return *reinterpret_cast<const int64_t*>(base + T1Layout<L16>::off(j) + r * 8); }
+  __device__ __forceinline__ double f64(int j) const { return *reinterpret_cast<const double*>(base + T1Layout<L16>::off(j) + r * 8); }
+};
+
 // ---- the Table 1 converter: fixed digit plan, column order A B C D E F G H cotC I J K ----
 // slots: 0 ones | 1 B | 2 C | 3 D | 4 E | 5 G | 6 H | 7 K | 8-9 F | 10-11 I | 12-16 A |
 //        17-23 cotC (signed, top byte 23) | 24-30 J | 31 zero
 // The field checks below are exactly the ranges those digit fields can carry.
 template <bool L16>
 struct ConvT1 {
+  __device__ __forceinline__ static SmemT1Src<L16> smem_src(const uint8_t* st, const ExactParams&, int r) {
+    return SmemT1Src<L16>{st, r};
+  }
   template <class Src>
   __device__ __forceinline__ static void row(const ExactParams& P, const Src& src, uint32_t (&w)[16],
                                              uint32_t& bad) {
@@ -95,8 +119,8 @@ struct ConvT1 {
     const int ec = dbl_exp_field(cot), ej = dbl_exp_field(J);
     const uint64_t uj = static_cast<uint64_t>(__double_as_longlong(J));
     bad |= (ec > P.real_emax[8]) | (ej > P.real_emax[10]) | ((uj >> 63) & ((uj << 1) != 0));  // J >= 0
-    const uint64_t qc = static_cast<uint64_t>(fixed_rn(cot, P.real_shift[8]));
-    const uint64_t qj = static_cast<uint64_t>(fixed_rn(J, P.real_shift[10]));
+    const uint64_t qc = fixed_rn<true>(cot, P.real_shift[8]);
+    const uint64_t qj = fixed_rn<false>(J, P.real_shift[10]);
     const uint32_t qclo = static_cast<uint32_t>(qc), qchi = static_cast<uint32_t>(qc >> 32) ^ 0x00800000u;
     const uint32_t qjlo = static_cast<uint32_t>(qj), qjhi = static_cast<uint32_t>(qj >> 32);
     constexpr uint32_t M = 0x64646464u;  // bytes of the f16 exponent 0x64
@@ -126,12 +150,15 @@ __device__ __forceinline__ int64_t load_as_int(const ExactParams& P, const Src& 
     case I16: return src.i16(j);
     case I32: return src.i32(j);
     case I64: return src.i64(j);
-    case F32: return fixed_rn(static_cast<double>(src.f32(j)), P.real_shift[j]);
-    default: return fixed_rn(src.f64(j), P.real_shift[j]);
+    case F32: return static_cast<int64_t>(fixed_rn<true>(static_cast<double>(src.f32(j)), P.real_shift[j]));
+    default: return static_cast<int64_t>(fixed_rn<true>(src.f64(j), P.real_shift[j]));
   }
 }
 
 struct ConvGeneric {
+  __device__ __forceinline__ static SmemSrc smem_src(const uint8_t* st, const ExactParams& P, int r) {
+    return SmemSrc{st, &P, r};
+  }
   template <class Src>
   __device__ __forceinline__ static uint32_t byte_of(const ExactParams& P, const Src& src, int c, int b, int sg) {
     if (c == -1) return 1u;
@@ -323,8 +350,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
           GlobalSrc src{&P, row0 + r};
           Conv::row(P, src, w, bad);
         } else if (r < valid) {
-          SmemSrc src{st, &P, r};
-          Conv::row(P, src, w, bad);
+          Conv::row(P, Conv::smem_src(st, P, r), w, bad);
         } else {
 #pragma unroll
           for (int q = 0; q < 16; ++q) w[q] = 0u;

@@ -58,6 +58,8 @@ struct ExactParams {
 constexpr int kExactWarps = 15;                 // consumer warps; +1 producer warp
 constexpr int kExactThreads = (kExactWarps + 1) * 32;
 constexpr int kExactTile = kExactWarps * 64;    // 960 rows per stage
+// Bytes one column of `elem_bytes`-byte values takes in a pipeline stage (128-byte granules).
+__host__ __device__ constexpr int stage_col_bytes(int elem_bytes) { return ((kExactTile * elem_bytes + 127) / 128) * 128; }
 size_t exact_smem_bytes(int stages, int stage_bytes);
 cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream);
 int exact_max_active_blocks(int conv, int stages, int stage_bytes);
