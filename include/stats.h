@@ -244,6 +244,44 @@ stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32
 /* Bytes per row of a Table 1 layout (60 or 44), or 0 for an unknown layout. */
 int32_t stats_table1_row_bytes(int32_t layout);
 
+/* ---------------------------------------------------------------------------
+ * No-allocation variant of the exact pass.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * running while a stream is captured into a CUDA graph under the global capture
+ * mode, where cudaMalloc is not allowed, or an application that keeps a fixed
+ * device budget and lets no library allocate outside it.
+ *
+ * It computes (n, s, S) of nrows rows (dcols: host array of cfg->p device
+ * pointers, as for stats_accumulate) with the exact pass and writes them to the
+ * caller's DEVICE buffer d_result of STATS_NOALLOC_RESULT_BYTES(p) bytes
+ * (8-byte aligned), laid out in 8-byte slots:
+ *   [0]                 n (int64)
+ *   [1, 1+p)            s, rounded once to double
+ *   [1+p, 1+p+T)        S packed upper, rounded once to double      (T = p(p+1)/2)
+ *   next 2p slots       s exact as stats_i128 (integer-valued columns; 0 for reals)
+ *   next 2T slots       S exact as stats_i128 (both columns integer-valued; 0 otherwise)
+ *   next 8 slots        flags: slot 0 = 1.0 if an exact entry does not fit 128 bits;
+ *                       slot 4 (low 32 bits) = device status bits of the pass:
+ *                       1 = a value outside its digit field (the sums are invalid),
+ *                       2 = a bounded wait expired.
+ * cfg must be STATS_EXACT with p <= 16 columns and a digit plan of at most
+ * STATS_EXACT_MAX_DIGITS digits; nrows <= 2^46.  Larger sizes return STATS_EINVAL.
+ * Each call computes the statistics of its own rows (no accumulation across calls).
+ *
+ * Scratch: a file-scope device array of 16,640 bytes inside the library, present
+ * on every GPU that loads the library until the process exits.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) once; make that
+ * first call before any stream capture begins.  All calls share the one array:
+ * each call clears it first, and calls whose work overlaps on the GPU (for
+ * example on two streams) race on it and must be serialised by the caller.
+ * Asynchronous on stream; results are valid once the stream reaches them.
+ * Errors: EINVAL (configuration, sizes beyond the maximum, NULL or misaligned
+ * pointers), ECUDA. */
+#define STATS_NOALLOC_RESULT_BYTES(p) (8 * (9 + 3 * (p) + 3 * ((p) * ((p) + 1) / 2)))
+stats_status stats_pass_noalloc(const stats_config* cfg, const void* const* dcols, int64_t nrows, void* d_result,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -343,3 +343,51 @@ def gen_table1(seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0,
     stats_gen_table1(seed, row0, nrows, layout, cols, stream)
     return cols
 
+
+# ----------------------------------------------------------------------------- no-allocation variant
+def noalloc_result_bytes(p: int) -> int:
+    """STATS_NOALLOC_RESULT_BYTES(p) of stats.h."""
+    return 8 * (9 + 3 * p + 3 * (p * (p + 1) // 2))
+
+
+def stats_pass_noalloc(cfg: Config, dcols: Sequence, nrows: int, d_result, stream=None):
+    """The exact pass without a context or any device allocation; writes (n, s, S)
+    into the caller's device buffer d_result (noalloc_result_bytes(p) bytes)."""
+    L = load()
+    if not hasattr(L, "_noalloc_ready"):
+        L.stats_pass_noalloc.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]
+        L.stats_pass_noalloc.restype = ctypes.c_int
+        L._noalloc_ready = True
+    s = cfg.c_struct()
+    arr = _ptr_array(dcols) if nrows > 0 else None
+    _check(L.stats_pass_noalloc(ctypes.byref(s), arr, nrows, _ptr(d_result), _stream_handle(stream)),
+           "stats_pass_noalloc")
+
+
+def parse_noalloc_result(buf: bytes, p: int) -> Raw:
+    """Decode a host copy of the stats_pass_noalloc result buffer."""
+    T = p * (p + 1) // 2
+    w = np.frombuffer(buf, dtype=np.int64)
+    d = np.frombuffer(buf, dtype=np.float64)
+    n = int(w[0])
+    s = d[1:1 + p].copy()
+    Su = d[1 + p:1 + p + T]
+    off = 1 + p + T
+    s_ex = [(int(w[off + 2 * j + 1]) << 64) + (int(w[off + 2 * j]) & 0xFFFFFFFFFFFFFFFF) for j in range(p)]
+    off += 2 * p
+    S_ex_u = [(int(w[off + 2 * t + 1]) << 64) + (int(w[off + 2 * t]) & 0xFFFFFFFFFFFFFFFF) for t in range(T)]
+    off += 2 * T
+    flags = off
+    status = int(np.frombuffer(buf[8 * (flags + 4):8 * (flags + 4) + 4], dtype=np.uint32)[0])
+    S = np.zeros((p, p))
+    SE = [[0] * p for _ in range(p)]
+    t = 0
+    for j in range(p):
+        for k in range(j, p):
+            S[j, k] = S[k, j] = Su[t]
+            SE[j][k] = SE[k][j] = S_ex_u[t]
+            t += 1
+    code = STATS_ERANGE if status & 1 else STATS_ETIMEOUT if status & 2 else \
+        STATS_EOVERFLOW if d[flags] != 0.0 else STATS_OK
+    return Raw(n, s, S, s_ex, SE, code)

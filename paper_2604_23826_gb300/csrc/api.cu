@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -792,3 +793,192 @@ stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// The no-allocation entry point.
+//
+// Some callers cannot allocate device memory: code that runs while a stream is
+// being captured into a CUDA graph under the global capture mode (where
+// cudaMalloc is not permitted), or a host application that owns a fixed device
+// memory budget and forbids any library from allocating outside it.  For them
+// stats_pass_noalloc runs the exact pass and the recombination of (n, s, S)
+// without a context: its scratch -- the digit Gram of one call, the per-call
+// staging accumulator and the ticket / error / status words -- lives in the
+// file-scope device array below (16,640 bytes, held by every GPU that loads the
+// library until the process exits).  The caller still passes the inputs and
+// the result buffer.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocWords = 2 * kDigits * kDigits + 32;  // 16,640 bytes
+constexpr int64_t kNoallocMaxRows = int64_t(1) << 46;      // digit sums stay far below 2^63
+
+__device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (a host-side reference to the array is not a device address).
+cudaError_t noalloc_scratch(unsigned long long** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned long long*>(g_noalloc_addr[dev]);
+  return cudaSuccess;
+}
+
+// The digit plan of a configuration, into fixed-size arrays (no heap use).
+stats_status noalloc_plan(const stats_config* cfg, ColPlan (&cp)[kMaxCols], ExactParams& xp, int& conv) {
+  const int p = cfg->p;
+  const bool bounded = cfg->lo != nullptr;
+  for (int j = 0; j < p; ++j) {
+    const int32_t dt = cfg->dtypes[j];
+    if (dt < I16 || dt > F64) return STATS_EINVAL;
+    cp[j] = ColPlan{};
+    const double lo = bounded ? cfg->lo[j] : 0.0, hi = bounded ? cfg->hi[j] : 0.0;
+    const bool ok = (dt == F32 || dt == F64) ? real_field(bounded, lo, hi, cp[j]) : int_field(dt, bounded, lo, hi, cp[j]);
+    if (!ok) return STATS_EINVAL;
+  }
+  static const int32_t l32[12] = {I64, I32, I32, I32, I32, I32, I32, I32, F64, I32, F64, I32};
+  static const int32_t l16[12] = {I64, I16, I16, I16, I16, I32, I16, I16, F64, I16, F64, I16};
+  conv = CONV_GENERIC;
+  for (int layout = 0; layout < 2 && p == 12; ++layout) {
+    const int32_t* want = layout ? l16 : l32;
+    bool match = true;
+    for (int j = 0; j < 12; ++j) match = match && cfg->dtypes[j] == want[j];
+    for (int j : {1, 2, 3, 4, 6, 7, 11}) match = match && !cp[j].is_signed && cp[j].k == 1;
+    for (int j : {5, 9}) match = match && !cp[j].is_signed && cp[j].k <= 2;
+    match = match && !cp[0].is_signed && cp[0].k <= 5 && cp[8].is_real && cp[8].is_signed && cp[10].is_real &&
+            !cp[10].is_signed;
+    if (match) {
+      conv = layout ? CONV_T1_L16 : CONV_T1_L32;
+      static const int off[12] = {12, 1, 2, 3, 4, 8, 5, 6, 17, 10, 24, 7};
+      static const int kk[12] = {5, 1, 1, 1, 1, 2, 1, 1, 7, 2, 7, 1};
+      for (int j = 0; j < 12; ++j) {
+        cp[j].off = off[j];
+        cp[j].k = kk[j];
+      }
+      break;
+    }
+  }
+  if (conv == CONV_GENERIC) {
+    int slot = 1;
+    for (int j = 0; j < p; ++j) {
+      cp[j].off = slot;
+      slot += cp[j].k;
+    }
+    if (slot > kDigits) return STATS_EINVAL;
+    for (int q = 0; q < kDigitPairs; ++q) {
+      xp.pc0[q] = xp.pc1[q] = -2;
+      xp.pb0[q] = xp.pb1[q] = 0;
+      xp.ps0[q] = xp.ps1[q] = 0;
+    }
+    xp.pc0[0] = -1;
+    for (int j = 0; j < p; ++j)
+      for (int a = 0; a < cp[j].k; ++a) {
+        const int s = cp[j].off + a, q = s / 2;
+        const int8_t sg = (cp[j].is_signed && a == cp[j].k - 1) ? 1 : 0;
+        if (s & 1) {
+          xp.pc1[q] = static_cast<int8_t>(j);
+          xp.pb1[q] = static_cast<int8_t>(a);
+          xp.ps1[q] = sg;
+        } else {
+          xp.pc0[q] = static_cast<int8_t>(j);
+          xp.pb0[q] = static_cast<int8_t>(a);
+          xp.ps0[q] = sg;
+        }
+      }
+  }
+  int off = 0;
+  for (int j = 0; j < p; ++j) {
+    const int b = dtype_bytes(cfg->dtypes[j]);
+    xp.dtype[j] = cfg->dtypes[j];
+    xp.col_bytes[j] = b;
+    xp.col_off[j] = off;
+    off += stage_col_bytes(b);
+    xp.real_shift[j] = cp[j].shift;
+    xp.real_emax[j] = cp[j].emax;
+    xp.kbytes[j] = cp[j].k;
+    xp.is_signed[j] = cp[j].is_signed;
+  }
+  xp.p = p;
+  xp.stage_bytes = off;
+  xp.stages = exact_smem_bytes(3, off) > 226 * 1024 ? 2 : 3;
+  if (exact_smem_bytes(xp.stages, off) > 226 * 1024) return STATS_EINVAL;
+  return STATS_OK;
+}
+
+}  // namespace
+
+extern "C" stats_status stats_pass_noalloc(const stats_config* cfg, const void* const* dcols, int64_t nrows,
+                                           void* d_result, void* stream) {
+  if (!cfg || !cfg->dtypes || cfg->mode != STATS_EXACT || cfg->p < 1 || cfg->p > kMaxCols) return STATS_EINVAL;
+  if ((cfg->lo == nullptr) != (cfg->hi == nullptr)) return STATS_EINVAL;
+  if (nrows < 0 || nrows > kNoallocMaxRows) return STATS_EINVAL;
+  if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 7u)) return STATS_EINVAL;
+  if (nrows > 0 && !dcols) return STATS_EINVAL;
+  for (int j = 0; j < cfg->p && nrows > 0; ++j)
+    if (!dcols[j] || (reinterpret_cast<uintptr_t>(dcols[j]) % dtype_bytes(cfg->dtypes[j])) != 0)
+      return STATS_EINVAL;
+  ColPlan cp[kMaxCols];
+  ExactParams P{};
+  int conv = CONV_GENERIC;
+  stats_status s = noalloc_plan(cfg, cp, P, conv);
+  if (s != STATS_OK) return s;
+  unsigned long long* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return STATS_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // every call shares the array: clear the accumulators and words that must start at zero
+  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * kNoallocWords, st) != cudaSuccess) return STATS_ECUDA;
+  unsigned int* words = reinterpret_cast<unsigned int*>(scratch + 2 * kDigits * kDigits);
+  P.call_acc = scratch;
+  P.acc = reinterpret_cast<long long*>(scratch + kDigits * kDigits);
+  P.ticket = words;
+  P.err = words + 1;
+  P.status = words + 2;
+  if (nrows > 0) {
+    P.direct = 0;
+    for (int j = 0; j < cfg->p; ++j) {
+      P.cols[j] = dcols[j];
+      if (!aligned16(dcols[j])) P.direct = 1;
+    }
+    P.nrows = nrows;
+    P.nmain = P.direct ? nrows : (nrows & ~int64_t(7));
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return STATS_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per = std::max(1, exact_max_active_blocks(conv, P.stages, P.stage_bytes));
+    const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
+    const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(sms, 1)) * per,
+                                                        std::max<int64_t>(tiles, 1)));
+    if (launch_exact(P, conv, grid, st) != cudaSuccess) return STATS_ECUDA;
+  }
+  // recombination into the caller's buffer (all columns flagged identifiers: raw outputs only)
+  FinalParams F{};
+  F.p = cfg->p;
+  F.mode = 0;
+  for (int j = 0; j < cfg->p; ++j) {
+    F.col[j].off = cp[j].off;
+    F.col[j].k = cp[j].k;
+    F.col[j].shift = cp[j].shift;
+    F.col[j].is_real = cp[j].is_real;
+    F.col[j].is_ident = 1;
+  }
+  F.g = P.acc;
+  F.out = static_cast<double*>(d_result);
+  if (launch_finalize(F, st) != cudaSuccess) return STATS_ECUDA;
+  const FinalLayout L = final_layout(cfg->p, 0);
+  double* status_slot = static_cast<double*>(d_result) + L.flags + 4;
+  if (cudaMemsetAsync(status_slot, 0, sizeof(double), st) != cudaSuccess) return STATS_ECUDA;
+  if (cudaMemcpyAsync(status_slot, P.status, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return STATS_ECUDA;
+  return STATS_OK;
+}
