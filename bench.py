@@ -35,14 +35,15 @@ UNIT = "rows/s"
 SEED = 1
 BYTES_PER_ROW = {0: 60, 1: 44}
 
-# DRAM traffic per row of the exact pass, from one ncu capture (see profiles/), with the
-# hash of the kernel sources it was taken on; null when the sources have changed since.
-NCU_TRAFFIC = {"bytes_per_row": None, "src_hash": None}
+# DRAM traffic per row of the exact pass (dram__bytes_read.sum + dram__bytes_write.sum over
+# the rows of one ncu capture, profiles/exact_pass_table1_L32_n1e8.md), with the hash of the
+# kernel sources it was taken on; reported as null once those sources change.
+NCU_TRAFFIC = {"bytes_per_row": 60.038, "src_hash": "1a0f244cd171ac78"}
 
 
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_exact.cu", "common.cuh", "kernels.h"):
+    for f in ("k_exact.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2604_23826_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -312,11 +313,26 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             h1.record(stream)
             torch.cuda.synchronize()
             e2e_ms = h0.elapsed_time(h1) / k_e2e
+            # the link's own rate: one pinned 4 GiB host -> device copy (the e2e path's roofline)
+            probe_h = host[0].view(torch.uint8)[: min(host[0].numel() * host[0].element_size(), 1 << 32)]
+            probe_d = torch.empty_like(probe_h, device=dev)
+            probe_d.copy_(probe_h, non_blocking=True)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            probe_d.copy_(probe_h, non_blocking=True)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            h2d_gbs = probe_h.numel() / (c0.elapsed_time(c1) / 1e3) / 1e9
+            del probe_d
             pa = 11
             T = 12 * 13 // 2
             result_bytes = 8 * (1 + 12 + T + 2 * 12 + 2 * T + pa + 3 * pa * pa + pa + 8) + 8 + 4
             e2e = {"value": n_e2e / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n_e2e * bpr,
                    "d2h_bytes_per_step": result_bytes, "rows": n_e2e, "ms_per_step": e2e_ms, "steps": k_e2e,
+                   "h2d_GBps_achieved": n_e2e * bpr / (e2e_ms / 1e3) / 1e9, "h2d_GBps_measured_copy": h2d_gbs,
+                   "h2d_frac": (n_e2e * bpr / (e2e_ms / 1e3) / 1e9) / h2d_gbs,
                    "api": "stats_accumulate_host (pinned host columns, double-buffered chunks) + stats_finalize"}
             del host
         else:

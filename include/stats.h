@@ -66,12 +66,14 @@ typedef enum { STATS_I16 = 0, STATS_I32 = 1, STATS_I64 = 2, STATS_F32 = 3, STATS
  *                      before it can round (all products and partial sums are exact
  *                      integers below 2^24).  Centering in exact integer arithmetic.
  *   STATS_FP64         the plain FP64 CUDA-core kernel with raw moments, as in the
- *                      paper (covariance = (S - s s^T / n) / (n - 1) in FP64).
+ *                      paper (covariance = (S - s s^T / n) / (n - 1) in FP64); a
+ *                      row-parallel kernel for p <= 12, a tiled one above.
  *   STATS_FP64_SHIFTED FP64 CUDA cores on x - c, c = the first row accumulated.
  *   STATS_BF16X3       FP32 data: x - c split into bf16 h + l; S ~ H^T H + H^T L + L^T H
  *                      on tensor cores, FP32 accumulation flushed to FP64.
  *   STATS_BF16X4       as BF16X3 plus L^T L.
- *   STATS_FP32         FP32 CUDA-core FMA on x - c, flushed to FP64.               */
+ *   STATS_FP32         FP32 CUDA-core FMA on x - c, flushed into FP32 (hi, lo) pairs.
+ * The BF16 modes take FP32 columns only; the others take any dtype.             */
 typedef enum {
   STATS_EXACT = 0,
   STATS_FP64 = 1,
@@ -142,6 +144,18 @@ stats_status stats_accumulate(stats_ctx* ctx, const void* const* dcols, int64_t 
 stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int64_t nrows, int64_t chunk_rows,
                                    void* stream);
 
+/* Many independent tables in one pass: table t (ctx ctxs[t], nrows[t] rows, dcols[t]
+ * a host array of ctxs[t]'s p device column pointers) is added to ctxs[t].  Tables
+ * of STATS_BF16X3 / STATS_BF16X4 contexts run together in one persistent launch per
+ * tile width (32 or 64 columns) and mode, each block taking one (table, tile, row
+ * range) unit from a device-side work list, larger units first; other contexts go
+ * through stats_accumulate one by one.  The descriptors are copied to a per-device
+ * workspace inside the library (grown on demand), so batched calls must be issued
+ * on one stream at a time.  A context appears at most once per call.
+ * Errors: as stats_accumulate. */
+stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, const void* const* const* dcols,
+                                      const int64_t* nrows, void* stream);
+
 /* dst += src, entry by entry, for two ctxs with identical configuration: the
  * combination of partial results from disjoint row subsets that the paper does
  * across its GPUs.  Exact for STATS_EXACT; FP64 modes add in double-double.
@@ -205,6 +219,12 @@ int32_t stats_num_analysis_columns(const stats_ctx* ctx);
  * pass kernels (0 = library default, a multiple of the SM count).  Results of
  * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
+
+/* Tuning knob of STATS_BF16X3 / STATS_BF16X4: rows a warp accumulates in the
+ * tensor cores' FP32 accumulators before adding them into its (hi, lo) pairs
+ * (16..4096, a multiple of 16; default 16 for p <= 64, else 64).  The FP32
+ * accumulation error grows about linearly with this interval.  Errors: EINVAL. */
+stats_status stats_set_flush_rows(stats_ctx* ctx, int32_t rows);
 
 /* ---------------------------------------------------------------------------
  * The paper's Table 1 workload (section "Background and Motivation", Table 1

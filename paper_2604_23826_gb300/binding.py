@@ -218,6 +218,21 @@ def stats_accumulate_host(ctx: Ctx, hcols: Sequence, nrows: int, chunk_rows: int
            "stats_accumulate_host")
 
 
+def stats_accumulate_batched(ctxs: Sequence[Ctx], dcols: Sequence[Sequence], nrows: Sequence[int], stream=None):
+    """Add table t (dcols[t]: its device columns, nrows[t] rows) to ctxs[t], all in one pass."""
+    L = load()
+    L.stats_accumulate_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_void_p)),
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    L.stats_accumulate_batched.restype = ctypes.c_int
+    n = len(ctxs)
+    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    arrays = [_ptr_array(cols) for cols in dcols]
+    outer = (ctypes.POINTER(ctypes.c_void_p) * n)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_void_p)) for a in arrays])
+    rows = (ctypes.c_int64 * n)(*nrows)
+    _check(L.stats_accumulate_batched(handles, n, outer, rows, _stream_handle(stream)), "stats_accumulate_batched")
+
+
 def stats_merge(dst: Ctx, src: Ctx):
     _check(load().stats_merge(dst.handle, src.handle), "stats_merge")
 
@@ -232,6 +247,13 @@ def stats_reset(ctx: Ctx):
 
 def stats_set_grid(ctx: Ctx, blocks: int):
     _check(load().stats_set_grid(ctx.handle, blocks), "stats_set_grid")
+
+
+def stats_set_flush_rows(ctx: Ctx, rows: int):
+    L = load()
+    L.stats_set_flush_rows.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.stats_set_flush_rows.restype = ctypes.c_int
+    _check(L.stats_set_flush_rows(ctx.handle, rows), "stats_set_flush_rows")
 
 
 def stats_num_analysis_columns(ctx: Ctx) -> int:

@@ -60,6 +60,14 @@ struct stats_ctx {
   long long* d_fn = nullptr;
   double* d_slots = nullptr;            // FP64 scratch: block slots + ticket
   int slot_grid = 0;
+  double* d_core_slots = nullptr;       // CUDA-core comparators (wide FP64, FP32) scratch
+  unsigned int* d_core_ticket = nullptr;
+  int core_grid = 0;
+  float* d_fshift = nullptr;            // BF16X3/X4: pivot as float
+  float* d_split_slots = nullptr;       // BF16X3/X4 scratch: warp slots
+  unsigned int* d_split_ticket = nullptr;
+  int split_grid = 0;
+  int flush_rows = 0;                   // 0: by table width
   bool shift_set = false;
   double* d_out = nullptr;              // finalize result
   double* d_work = nullptr;             // finalize scratch
@@ -266,6 +274,83 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
     int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
     CK(c, launch_exact(P, c->conv, g, st));
+  } else if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
+    SplitParams S{};
+    for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
+    S.p = c->p;
+    S.shift = c->d_fshift;
+    if (!c->shift_set) {
+      CK(c, launch_split_shift(S, c->d_shift, st));
+      c->shift_set = true;
+    }
+    const int T = split_tile(c->p);
+    S.nblk = (c->p + T - 1) / T;
+    S.ntiles = S.nblk * (S.nblk + 1) / 2;
+    const int64_t max_split = std::max<int64_t>(1, nrows / 4096);
+    S.ksplit = static_cast<int>(std::min<int64_t>(max_split, (4 * c->sms + S.ntiles - 1) / S.ntiles));
+    if (c->grid > 0) S.ksplit = std::max(1, c->grid / S.ntiles);
+    const int g = S.ntiles * S.ksplit;
+    if (!c->d_split_slots || c->split_grid < g) {
+      if (c->d_split_slots) CK(c, cudaFree(c->d_split_slots));
+      c->d_split_slots = nullptr;
+      const size_t bytes = split_slot_floats(g) * sizeof(float) + 256;
+      CK(c, cudaMalloc(&c->d_split_slots, bytes));
+      CK(c, cudaMemset(c->d_split_slots, 0, bytes));
+      c->split_grid = g;
+      c->d_split_ticket = reinterpret_cast<unsigned int*>(c->d_split_slots + split_slot_floats(g));
+    }
+    // FP32 tensor accumulation error grows with the rows summed before a flush (measured:
+    // about linear); narrow tables flush every 16 rows, wide ones (flush cost ~ p^2) every 64
+    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : (c->p <= 64 ? 16 : 64);
+    S.nrows = nrows;
+    S.slots = c->d_split_slots;
+    S.ticket = c->d_split_ticket;
+    S.acc_s = c->d_fs;
+    S.acc_s_lo = c->d_fs_lo;
+    S.acc_S = c->d_fS;
+    S.acc_S_lo = c->d_fS_lo;
+    S.acc_n = c->d_fn;
+    CK(c, launch_split(S, T, c->mode == STATS_BF16X4, g, st));
+  } else if (c->mode == STATS_FP32 || c->p > 12) {
+    // tiled CUDA-core pass: FP32-core, or FP64 for tables wider than the row kernel
+    CoreParams C{};
+    for (int j = 0; j < c->p; ++j) {
+      C.cols[j] = dcols[j];
+      C.dtype[j] = c->dtypes[j];
+    }
+    C.p = c->p;
+    if (c->mode != STATS_FP64) {
+      if (!c->shift_set) {
+        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, c->d_shift, st));
+        c->shift_set = true;
+      }
+      C.shift = c->d_shift;
+    }
+    C.nblk = (c->p + 63) / 64;
+    C.ntiles = C.nblk * (C.nblk + 1) / 2;
+    const int64_t max_split = std::max<int64_t>(1, nrows / 4096);
+    C.ksplit = static_cast<int>(std::min<int64_t>(max_split, (4 * c->sms + C.ntiles - 1) / C.ntiles));
+    if (c->grid > 0) C.ksplit = std::max(1, c->grid / C.ntiles);
+    const int g = C.ntiles * C.ksplit;
+    if (!c->d_core_slots || c->core_grid < g) {
+      if (c->d_core_slots) CK(c, cudaFree(c->d_core_slots));
+      c->d_core_slots = nullptr;
+      const size_t bytes = core_slot_doubles(g) * sizeof(double) + 256;
+      CK(c, cudaMalloc(&c->d_core_slots, bytes));
+      CK(c, cudaMemset(c->d_core_slots, 0, bytes));
+      c->core_grid = g;
+      c->d_core_ticket = reinterpret_cast<unsigned int*>(c->d_core_slots + core_slot_doubles(g));
+    }
+    C.flush_rows = c->flush_rows > 0 ? c->flush_rows : 64;
+    C.nrows = nrows;
+    C.slots = c->d_core_slots;
+    C.ticket = c->d_core_ticket;
+    C.acc_s = c->d_fs;
+    C.acc_s_lo = c->d_fs_lo;
+    C.acc_S = c->d_fS;
+    C.acc_S_lo = c->d_fS_lo;
+    C.acc_n = c->d_fn;
+    CK(c, launch_core(C, c->mode == STATS_FP32, g, st));
   } else {
     Fp64Params P{};
     for (int j = 0; j < c->p; ++j) {
@@ -314,7 +399,11 @@ stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
   F.fS = c->d_fS;
   F.fS_lo = c->d_fS_lo;
   F.fn = c->d_fn;
-  F.shift = (c->mode == STATS_FP64_SHIFTED && c->shift_set) ? c->d_shift : nullptr;
+  F.shift = ((c->mode == STATS_FP64_SHIFTED || c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4 ||
+              c->mode == STATS_FP32) &&
+             c->shift_set)
+                ? c->d_shift
+                : nullptr;
   F.out = c->d_out;
   F.work = c->d_work;
   cudaStream_t st = c->last;
@@ -330,6 +419,9 @@ void free_ctx(stats_ctx* c) {
   cudaFree(c->d_call);
   cudaFree(c->d_fs);
   cudaFree(c->d_slots);
+  cudaFree(c->d_fshift);
+  cudaFree(c->d_core_slots);
+  cudaFree(c->d_split_slots);
   cudaFree(c->d_out);
   cudaFree(c->d_work);
   if (c->h_out) cudaFreeHost(c->h_out);
@@ -349,8 +441,9 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
   if (cfg->mode < STATS_EXACT || cfg->mode > STATS_FP32) return STATS_EINVAL;
   if ((cfg->lo == nullptr) != (cfg->hi == nullptr)) return STATS_EINVAL;
   // modes not built yet: BF16X3 / BF16X4 / FP32
-  if (cfg->mode == STATS_BF16X3 || cfg->mode == STATS_BF16X4 || cfg->mode == STATS_FP32) return STATS_EINVAL;
-  if ((cfg->mode == STATS_FP64 || cfg->mode == STATS_FP64_SHIFTED) && cfg->p > 12) return STATS_EINVAL;
+  if (cfg->mode == STATS_BF16X3 || cfg->mode == STATS_BF16X4)
+    for (int j = 0; j < cfg->p; ++j)
+      if (cfg->dtypes[j] != F32) return STATS_EINVAL;  // the split path takes FP32 columns
   stats_ctx* c = new (std::nothrow) stats_ctx();
   if (!c) return STATS_ENOMEM;
   c->p = cfg->p;
@@ -402,9 +495,8 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
     }
     c->xp.p = c->p;
     c->xp.stage_bytes = off;
-    c->stages = 3;
-    if (exact_smem_bytes(3, off) > 226 * 1024) c->stages = 2;
-    if (exact_smem_bytes(c->stages, off) > 226 * 1024) {
+    c->stages = exact_pick_stages(off);
+    if (c->stages == 0) {
       delete c;
       return STATS_EINVAL;  // rows too wide for the pipeline
     }
@@ -443,6 +535,8 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
       c->d_fn = reinterpret_cast<long long*>(c->d_shift + c->p);
       c->d_status = reinterpret_cast<unsigned int*>(c->d_fn + 1);
     }
+    if (e == cudaSuccess && (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4))
+      e = cudaMalloc(&c->d_fshift, c->p * sizeof(float));
   }
   c->lay = final_layout(c->p, c->pa);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_out, c->lay.total * sizeof(double));
@@ -536,6 +630,158 @@ stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int
   return STATS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device workspace of batched launches (table descriptors, column-pointer arrays,
+// work units), grown as needed, one per device; batched calls are stream-ordered.
+struct BatchWorkspace {
+  void* dev = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_batch_mu;
+BatchWorkspace g_batch_ws[64];
+
+constexpr int64_t kBatchRowsPerUnit = int64_t(1) << 20;  // rows one block takes in a batched launch
+
+}  // namespace
+
+extern "C" {
+
+stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, const void* const* const* dcols,
+                                      const int64_t* nrows, void* stream) {
+  if (ntables < 0 || (ntables > 0 && (!ctxs || !dcols || !nrows))) return STATS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // tables not on the split path go one by one through stats_accumulate
+  std::vector<int> split_idx;
+  for (int t = 0; t < ntables; ++t) {
+    stats_ctx* c = ctxs[t];
+    stats_status s = check_sticky(c);
+    if (s != STATS_OK) return s;
+    if (nrows[t] < 0 || (nrows[t] > 0 && !dcols[t])) return STATS_EINVAL;
+    if (nrows[t] == 0) continue;
+    if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
+      for (int j = 0; j < c->p; ++j)
+        if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
+      split_idx.push_back(t);
+    } else {
+      s = stats_accumulate(c, dcols[t], nrows[t], stream);
+      if (s != STATS_OK) return s;
+    }
+  }
+  if (split_idx.empty()) return STATS_OK;
+  int dev = 0;
+  CK(ctxs[split_idx[0]], cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return STATS_EINVAL;
+  // host image: descriptors, then column-pointer arrays, then units
+  const size_t nt = split_idx.size();
+  size_t ncolptr = 0;
+  for (int t : split_idx) ncolptr += ctxs[t]->p;
+  std::vector<SplitParams> descs(nt);
+  std::vector<const float*> colptrs(ncolptr);
+  std::vector<int2> units[2][2];  // [T == 64][x4]
+  std::vector<int64_t> unit_rows[2][2];
+  const size_t off_cols = ((nt * sizeof(SplitParams) + 255) / 256) * 256;
+  const size_t off_units = off_cols + ((ncolptr * sizeof(void*) + 255) / 256) * 256;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchWorkspace& ws = g_batch_ws[dev];
+  size_t total_units = 0;
+  size_t cp = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    const int t = split_idx[i];
+    stats_ctx* c = ctxs[t];
+    SplitParams& S = descs[i];
+    S = SplitParams{};
+    S.p = c->p;
+    S.shift = c->d_fshift;
+    const int T = split_tile(c->p);
+    S.nblk = (c->p + T - 1) / T;
+    S.ntiles = S.nblk * (S.nblk + 1) / 2;
+    S.ksplit = static_cast<int>(std::max<int64_t>(1, (nrows[t] + kBatchRowsPerUnit - 1) / kBatchRowsPerUnit));
+    const int g = S.ntiles * S.ksplit;
+    if (!c->d_split_slots || c->split_grid < g) {
+      if (c->d_split_slots) CK(c, cudaFree(c->d_split_slots));
+      c->d_split_slots = nullptr;
+      const size_t bytes = split_slot_floats(g) * sizeof(float) + 256;
+      CK(c, cudaMalloc(&c->d_split_slots, bytes));
+      CK(c, cudaMemset(c->d_split_slots, 0, bytes));
+      c->split_grid = g;
+      c->d_split_ticket = reinterpret_cast<unsigned int*>(c->d_split_slots + split_slot_floats(g));
+    }
+    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : (c->p <= 64 ? 16 : 64);
+    S.nrows = nrows[t];
+    S.slots = c->d_split_slots;
+    S.ticket = c->d_split_ticket;
+    S.acc_s = c->d_fs;
+    S.acc_s_lo = c->d_fs_lo;
+    S.acc_S = c->d_fS;
+    S.acc_S_lo = c->d_fS_lo;
+    S.acc_n = c->d_fn;
+    for (int j = 0; j < c->p; ++j) colptrs[cp + j] = static_cast<const float*>(dcols[t][j]);
+    cp += c->p;
+    const int a = T == 64 ? 1 : 0, b = c->mode == STATS_BF16X4 ? 1 : 0;
+    for (int u = 0; u < g; ++u) {
+      units[a][b].push_back(make_int2(static_cast<int>(i), u));
+      unit_rows[a][b].push_back(nrows[t] / S.ksplit);
+    }
+    total_units += g;
+  }
+  const size_t need = off_units + total_units * sizeof(int2) + 256;
+  if (ws.bytes < need) {
+    if (ws.dev) CK(ctxs[split_idx[0]], cudaFree(ws.dev));
+    ws.dev = nullptr;
+    ws.bytes = 0;
+    CK(ctxs[split_idx[0]], cudaMalloc(&ws.dev, need));
+    ws.bytes = need;
+  }
+  char* base = static_cast<char*>(ws.dev);
+  // device column-pointer arrays, then descriptors pointing at them
+  cp = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    descs[i].col_ptrs = reinterpret_cast<const float* const*>(base + off_cols) + cp;
+    cp += descs[i].p;
+  }
+  // units, grouped by (T, mode), larger row ranges first
+  std::vector<int2> all_units;
+  size_t group_off[2][2], group_n[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      std::vector<size_t> order(units[a][b].size());
+      for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](size_t x, size_t y) { return unit_rows[a][b][x] > unit_rows[a][b][y]; });
+      group_off[a][b] = all_units.size();
+      group_n[a][b] = order.size();
+      for (size_t k : order) all_units.push_back(units[a][b][k]);
+    }
+  stats_ctx* c0 = ctxs[split_idx[0]];
+  CK(c0, cudaMemcpyAsync(base, descs.data(), nt * sizeof(SplitParams), cudaMemcpyHostToDevice, st));
+  CK(c0, cudaMemcpyAsync(base + off_cols, colptrs.data(), ncolptr * sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(c0, cudaMemcpyAsync(base + off_units, all_units.data(), all_units.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                         st));
+  // pivots of tables seen for the first time
+  for (size_t i = 0; i < nt; ++i) {
+    stats_ctx* c = ctxs[split_idx[i]];
+    if (!c->shift_set) {
+      SplitParams S = descs[i];
+      S.col_ptrs = nullptr;
+      for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[split_idx[i]][j]);
+      CK(c, launch_split_shift(S, c->d_shift, st));
+      c->shift_set = true;
+    }
+  }
+  const SplitParams* dtabs = reinterpret_cast<const SplitParams*>(base);
+  const int2* dunits = reinterpret_cast<const int2*>(base + off_units);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      if (group_n[a][b])
+        CK(c0, launch_split_batched(dtabs, dunits + group_off[a][b], static_cast<int>(group_n[a][b]), a ? 64 : 32,
+                                    b == 1, st));
+  for (int t : split_idx) ctxs[t]->last = st;
+  return STATS_OK;
+}
+
 stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
   stats_status s = check_sticky(dst);
   if (s != STATS_OK) return s;
@@ -548,7 +794,9 @@ stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
           dst->plan[j].shift != src->plan[j].shift || dst->plan[j].is_signed != src->plan[j].is_signed)
         return STATS_EINVAL;
   }
-  if (dst->mode == STATS_FP64_SHIFTED) return STATS_EINVAL;  // shifts of two ctxs generally differ
+  if (dst->mode == STATS_FP64_SHIFTED || dst->mode == STATS_BF16X3 || dst->mode == STATS_BF16X4 ||
+      dst->mode == STATS_FP32)
+    return STATS_EINVAL;  // the pivots of two ctxs generally differ
   if (src->last) CK(dst, cudaStreamSynchronize(src->last));
   stats_ctx* srcm = const_cast<stats_ctx*>(src);
   // carry src's device error bits over
@@ -758,6 +1006,12 @@ stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks) {
   return STATS_OK;
 }
 
+stats_status stats_set_flush_rows(stats_ctx* ctx, int32_t rows) {
+  if (!ctx || rows < 16 || rows > 4096 || (rows & 15)) return STATS_EINVAL;
+  ctx->flush_rows = rows;
+  return STATS_OK;
+}
+
 int32_t stats_table1_row_bytes(int32_t layout) {
   return layout == STATS_T1_L32 ? 60 : layout == STATS_T1_L16 ? 44 : 0;
 }
@@ -911,8 +1165,8 @@ stats_status noalloc_plan(const stats_config* cfg, ColPlan (&cp)[kMaxCols], Exac
   }
   xp.p = p;
   xp.stage_bytes = off;
-  xp.stages = exact_smem_bytes(3, off) > 226 * 1024 ? 2 : 3;
-  if (exact_smem_bytes(xp.stages, off) > 226 * 1024) return STATS_EINVAL;
+  xp.stages = exact_pick_stages(off);
+  if (xp.stages == 0) return STATS_EINVAL;
   return STATS_OK;
 }
 

@@ -43,7 +43,7 @@ struct ExactParams {
   int8_t pc1[kDigitPairs], pb1[kDigitPairs], ps1[kDigitPairs];
   int32_t p;
   int32_t direct;       // 1: some column is not 16-byte aligned -- consumers read global memory directly
-  int32_t stages;       // pipeline depth (2 or 3)
+  int32_t stages;       // pipeline depth (2..kExactMaxStages)
   int32_t stage_bytes;  // bytes of one stage (multiple of 128)
   int64_t nrows;        // rows of this call
   int64_t nmain;        // rows moved by bulk copies (nrows rounded down to a multiple of 8)
@@ -57,10 +57,13 @@ struct ExactParams {
 // Rows of one pipeline stage of the EXACT pass.
 constexpr int kExactWarps = 15;                 // consumer warps; +1 producer warp
 constexpr int kExactThreads = (kExactWarps + 1) * 32;
-constexpr int kExactTile = kExactWarps * 64;    // 960 rows per stage
+constexpr int kExactTile = kExactWarps * 64;    // 960 rows per stage, 64 per consumer warp
+constexpr int kExactMaxStages = 3;
 // Bytes one column of `elem_bytes`-byte values takes in a pipeline stage (128-byte granules).
 __host__ __device__ constexpr int stage_col_bytes(int elem_bytes) { return ((kExactTile * elem_bytes + 127) / 128) * 128; }
 size_t exact_smem_bytes(int stages, int stage_bytes);
+// Deepest pipeline (2..kExactMaxStages stages) whose shared memory fits one block, or 0.
+int exact_pick_stages(int stage_bytes);
 cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream);
 int exact_max_active_blocks(int conv, int stages, int stage_bytes);
 
@@ -84,6 +87,60 @@ cudaError_t launch_fp64(const Fp64Params& P, int grid, cudaStream_t stream);
 size_t fp64_slot_doubles(int grid);  // slots + ticket word, zeroed once at allocation
 cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, double* shift,
                              cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// FP32 tables on the tensor cores with a bf16 two-term split (BF16x3 / BF16x4).
+// ---------------------------------------------------------------------------
+struct SplitParams {
+  const float* cols[256];          // single-table launches: the column pointers
+  const float* const* col_ptrs;    // batched launches: device array of the column pointers
+  const float* shift;   // p floats (device): pivot c_j
+  int32_t p;
+  int32_t nblk;         // ceil(p / T)
+  int32_t ntiles;       // nblk (nblk + 1) / 2
+  int32_t ksplit;       // row ranges per tile
+  int32_t flush_rows;   // rows of a warp between FP32 -> (hi, lo) flushes
+  int64_t nrows;
+  float* slots;         // scratch: split_slot_floats(grid) floats
+  unsigned int* ticket; // scratch: block counter, zero between calls
+  double* acc_s;        // ctx accumulators (shifted sums), double-double
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+};
+size_t split_slot_floats(int grid);
+int split_tile(int p);  // T = 32 or 64
+cudaError_t launch_split(const SplitParams& P, int T, bool x4, int grid, cudaStream_t stream);
+cudaError_t launch_split_shift(const SplitParams& P, double* shift_d, cudaStream_t stream);
+// units[i] = (index into tabs, local block of that table); all tables share T and the mode
+cudaError_t launch_split_batched(const SplitParams* tabs, const int2* units, int nunits, int T, bool x4,
+                                 cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// CUDA-core comparators for any width: FP64 (raw / shifted) and FP32-core.
+// ---------------------------------------------------------------------------
+constexpr int kCoreSlotDoubles = 2 * (32 * 32 + 32);
+struct CoreParams {
+  const void* cols[256];
+  int32_t dtype[256];
+  const double* shift;  // p pivots or nullptr (raw moments)
+  int32_t p;
+  int32_t nblk;         // ceil(p / 64)
+  int32_t ntiles;
+  int32_t ksplit;
+  int32_t flush_rows;   // FP32 only: rows between flushes into (hi, lo) pairs
+  int64_t nrows;
+  double* slots;        // scratch: core_slot_doubles(grid)
+  unsigned int* ticket;
+  double* acc_s;
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+};
+size_t core_slot_doubles(int grid);
+cudaError_t launch_core(const CoreParams& P, bool fp32, int grid, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Finalize (one block): recombination, exact centering, cov / corr, Jacobi.

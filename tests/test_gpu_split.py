@@ -1,0 +1,167 @@
+"""FP32 tables through the bf16-split tensor-core modes (BF16x3, BF16x4), against
+the double-double oracle on the same float32 values.
+
+Inputs follow the shapes of the batched-tables and wide-table workloads:
+independent columns x ~ N(mu_j, sigma_j^2) with mu_j ~ U[1e3, 1e5] and
+sigma_j ~ U[0.1, 10] (a mean-to-spread ratio up to 1e6 stresses centering), and
+a correlated table X = Z L^T + mu with eigenvalues 1/k.  Generated on the host
+with numpy (seeded) and handed to both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+G = pytest.importorskip("paper_2604_23826_gb300")
+
+
+def independent_table(seed, n, p):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(1e3, 1e5, p)
+    sd = rng.uniform(0.1, 10.0, p)
+    return (mu + sd * rng.standard_normal((n, p))).astype(np.float32)
+
+
+def correlated_table(seed, n, p):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    cov = (q * (1.0 / np.arange(1, p + 1))) @ q.T
+    L = np.linalg.cholesky(cov)
+    mu = rng.uniform(0.0, 1e3, p)
+    return (rng.standard_normal((n, p)) @ L.T + mu).astype(np.float32)
+
+
+def run_mode(X, mode, flush_rows=None):
+    n, p = X.shape
+    cols = [torch.from_numpy(np.ascontiguousarray(X[:, j])).cuda() for j in range(p)]
+    cfg = G.Config([G.STATS_F32] * p, mode, [0] * p)
+    with G.stats_init(cfg) as ctx:
+        if flush_rows:
+            G.stats_set_flush_rows(ctx, flush_rows)
+        G.stats_accumulate(ctx, cols, n)
+        raw = G.stats_raw(ctx)
+        an = G.stats_finalize(ctx)
+    return raw, an
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("p", [8, 16, 32, 64])
+@pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
+def test_split_independent_columns(p, mode):
+    n = 200_003
+    X = independent_table(100 + p, n, p)
+    raw, an = run_mode(X, mode)
+    cols = [X[:, j].astype(np.float64) for j in range(p)]
+    cov = O.cov_twopass_columns(cols)
+    st = O.stats_columns(cols)
+    assert raw.n == n
+    err = rel_fro(an.cov, cov)
+    mean_err = float(np.max(np.abs(an.mean - st.s_float() / n) / np.abs(st.s_float() / n)))
+    print(f"\nmode={mode} p={p}: cov rel-Frobenius error {err:.3e}, mean rel error {mean_err:.3e}")
+    assert mean_err < 1e-9
+    # BF16x4 meets 2e-6; BF16x3 drops l l^T (|l| <= 2^-8 |r| for bf16), a bias up to ~2^-16 relative
+    assert err < (2e-6 if mode == G.STATS_BF16X4 else 3e-5)
+
+
+@pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
+def test_split_correlated_wide(mode):
+    n, p = 40_000, 256
+    X = correlated_table(4, n, p)
+    raw, an = run_mode(X, mode)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    err = rel_fro(an.cov, cov)
+    ev_ref = np.linalg.eigvalsh(cov)[::-1][:10]
+    ev_err = float(np.max(np.abs(an.evals[:10] - ev_ref) / ev_ref))
+    print(f"\nmode={mode} p=256: cov rel-Frobenius error {err:.3e}, top-10 eigenvalue rel error {ev_err:.3e}")
+    assert err < (2e-6 if mode == G.STATS_BF16X4 else 3e-5)
+    assert ev_err < 1e-4
+
+
+@pytest.mark.parametrize("flush", [16, 32, 64, 256])
+def test_split_flush_interval_sweep(flush):
+    """Error of both modes against the flush interval of the FP32 tensor accumulators (reported)."""
+    n, p = 200_003, 8
+    X = independent_table(108, n, p)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    for mode in (G.STATS_BF16X3, G.STATS_BF16X4):
+        _, an = run_mode(X, mode, flush)
+        print(f"\nflush={flush} mode={mode} p={p}: cov rel-Frobenius error {rel_fro(an.cov, cov):.3e}")
+
+
+# --------------------------------------------------------------------------- CUDA-core comparators, any width
+@pytest.mark.parametrize("p", [13, 40, 256])
+def test_wide_fp64_modes(p):
+    """FP64 (raw and shifted) on tables wider than the row-parallel kernel: the tiled pass."""
+    n = 30_011 if p == 256 else 100_003
+    X = correlated_table(7 + p, n, p).astype(np.float64)
+    cols64 = [np.ascontiguousarray(X[:, j]) for j in range(p)]
+    st = O.stats_columns(cols64)
+    cov = O.cov_twopass_columns(cols64)
+    S = st.S_float()
+    for mode in (G.STATS_FP64, G.STATS_FP64_SHIFTED):
+        dev = [torch.from_numpy(c).cuda() for c in cols64]
+        cfg = G.Config([G.STATS_F64] * p, mode, [0] * p)
+        with G.stats_init(cfg) as ctx:
+            G.stats_accumulate(ctx, dev, n)
+            raw = G.stats_raw(ctx)
+            an = G.stats_finalize(ctx)
+        assert raw.n == n
+        assert rel_fro(raw.S, S) < 1e-13, mode
+        assert np.max(np.abs(raw.s - st.s_float()) / np.abs(st.s_float())) < 1e-13
+        err = rel_fro(an.cov, cov)
+        print(f"\nFP64 mode={mode} p={p}: cov rel-Frobenius error {err:.3e}")
+        # raw moments (S - s s^T / n) cancel: with mean/spread up to 1e3 the paper's formula
+        # loses ~6 digits to rounding; the shifted pass keeps full precision
+        assert err < (1e-6 if mode == G.STATS_FP64 else 1e-12)
+
+
+@pytest.mark.parametrize("p", [8, 64, 256])
+def test_fp32_core_mode(p):
+    """The FP32 CUDA-core comparator (shifted): error reported against the oracle."""
+    n = 40_000 if p == 256 else 200_003
+    X = correlated_table(11, n, p) if p == 256 else independent_table(200 + p, n, p)
+    raw, an = run_mode(X, G.STATS_FP32)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    err = rel_fro(an.cov, cov)
+    print(f"\nFP32-core p={p}: cov rel-Frobenius error {err:.3e}")
+    assert raw.n == n
+    assert err < 1e-4
+
+
+# --------------------------------------------------------------------------- batched tables
+def test_batched_many_tables_one_pass():
+    """Independent FP32 tables of uneven sizes and widths in one batched call (two calls in a row),
+    each table against the oracle; p in {8, 16, 32, 64}, rows log-uniform."""
+    rng = np.random.default_rng(3)
+    ntab = 48
+    ps = rng.choice([8, 16, 32, 64], ntab)
+    ns = np.exp(rng.uniform(np.log(1e3), np.log(1.2e5), ntab)).astype(np.int64)
+    tables = [independent_table(1000 + t, int(ns[t]), int(ps[t])) for t in range(ntab)]
+    ctxs = [G.stats_init(G.Config([G.STATS_F32] * int(ps[t]), G.STATS_BF16X4, [0] * int(ps[t])))
+            for t in range(ntab)]
+    halves = []
+    for part in range(2):  # the first and second halves of every table, in two batched calls
+        dev, rows = [], []
+        for t, X in enumerate(tables):
+            h = X.shape[0] // 2
+            Xp = X[:h] if part == 0 else X[h:]
+            dev.append([torch.from_numpy(np.ascontiguousarray(Xp[:, j])).cuda() for j in range(Xp.shape[1])])
+            rows.append(Xp.shape[0])
+        halves.append(dev)
+        G.stats_accumulate_batched(ctxs, dev, rows)
+    worst = 0.0
+    for t, X in enumerate(tables):
+        an = G.stats_finalize(ctxs[t])
+        raw = G.stats_raw(ctxs[t])
+        assert raw.n == X.shape[0]
+        cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(X.shape[1])])
+        worst = max(worst, rel_fro(an.cov, cov))
+        ctxs[t].close()
+    print(f"\nbatched BF16x4, {ntab} tables: worst cov rel-Frobenius error {worst:.3e}")
+    assert worst < 2e-6
