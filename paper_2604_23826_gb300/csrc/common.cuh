@@ -140,6 +140,20 @@ __device__ __forceinline__ uint32_t digits2(uint32_t packed_bytes, uint32_t bias
   return half2_sub(packed_bytes | kH1024, bias);
 }
 
+__device__ __forceinline__ uint32_t half2_mul(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+// Two small non-negative integers x, y < 256 to an f16x2 of (x, y) on the FMA
+// pipe only: x + 65536 y (one IMAD) holds each value as the bit pattern of the
+// subnormal half v * 2^-24; two exact multiplications by 2^12 rescale it to v.
+__device__ __forceinline__ uint32_t small_pair_f16x2(uint32_t x, uint32_t y) {
+  const uint32_t bits = y * 65536u + x;
+  constexpr uint32_t k2p12 = 0x6C006C00u;  // {4096, 4096}
+  return half2_mul(half2_mul(bits, k2p12), k2p12);
+}
+
 // ---------------------------------------------------------------------------
 // Fixed point of a double: q = round(x * 2^sh) as a two's complement int64,
 // ties rounded up in magnitude, with 32-bit integer operations only (no FP64

@@ -5,7 +5,7 @@
 // Every row becomes a vector w of 32 small integer "digits": the ones column
 // (so that n and s fall out of the same product), then each column's value split
 // into base-256 digits (integers directly; real columns first as a fixed-point
-// integer q = round(x * 2^shift) of their declared range, ties away from zero).  The digit Gram matrix
+// integer q = round(x * 2^shift) of their declared range).  The digit Gram matrix
 // G = sum_rows w w^T is accumulated on the tensor cores with f16 operands
 // (every digit |d| <= 255 is exact in f16) and FP32 accumulators.  Each product
 // is below 2^16 and a warp flushes its accumulators every 256 of its rows, so
@@ -89,6 +89,18 @@ struct SmemT1Src {
   __device__ __forceinline__ double f64(int j) const { return *reinterpret_cast<const double*>(base + T1Layout<L16>::off(j) + r * 8); }
 };
 
+// The Table 1 real columns convert on the FP64 unit: q = round-to-nearest-even(x * 2^sh),
+// the scaling an exponent-field add (exact), zero and subnormal inputs giving 0.  (The
+// integer-only fixed_rn keeps the ALU pipe busier; on sm_103a the FP64 conversion
+// unit sustains about two per clock per SM, well above what this pass needs.)
+__device__ __forceinline__ uint64_t fixed_f2i(double x, int sh) {
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x)), lo = static_cast<uint32_t>(__double2loint(x));
+  const bool normal = ((hi >> 20) & 0x7FF) != 0;
+  const long long q =
+      __double2ll_rn(__hiloint2double(static_cast<int>(hi + (static_cast<uint32_t>(sh) << 20)), static_cast<int>(lo)));
+  return normal ? static_cast<uint64_t>(q) : 0ull;
+}
+
 // ---- the Table 1 converter: fixed digit plan, column order A B C D E F G H cotC I J K ----
 // slots: 0 ones | 1 B | 2 C | 3 D | 4 E | 5 G | 6 H | 7 K | 8-9 F | 10-11 I | 12-16 A |
 //        17-23 cotC (signed, top byte 23) | 24-30 J | 31 zero
@@ -119,15 +131,15 @@ struct ConvT1 {
     const int ec = dbl_exp_field(cot), ej = dbl_exp_field(J);
     const uint64_t uj = static_cast<uint64_t>(__double_as_longlong(J));
     bad |= (ec > P.real_emax[8]) | (ej > P.real_emax[10]) | ((uj >> 63) & ((uj << 1) != 0));  // J >= 0
-    const uint64_t qc = fixed_rn<true>(cot, P.real_shift[8]);
-    const uint64_t qj = fixed_rn<false>(J, P.real_shift[10]);
+    const uint64_t qc = fixed_f2i(cot, P.real_shift[8]);
+    const uint64_t qj = fixed_f2i(J, P.real_shift[10]);
     const uint32_t qclo = static_cast<uint32_t>(qc), qchi = static_cast<uint32_t>(qc >> 32) ^ 0x00800000u;
     const uint32_t qjlo = static_cast<uint32_t>(qj), qjhi = static_cast<uint32_t>(qj >> 32);
     constexpr uint32_t M = 0x64646464u;  // bytes of the f16 exponent 0x64
-    w[0] = digits2(1u | (static_cast<uint32_t>(B) << 16));
-    w[1] = digits2(static_cast<uint32_t>(C) | (static_cast<uint32_t>(D) << 16));
-    w[2] = digits2(static_cast<uint32_t>(E) | (static_cast<uint32_t>(G) << 16));
-    w[3] = digits2(static_cast<uint32_t>(H) | (static_cast<uint32_t>(K) << 16));
+    w[0] = small_pair_f16x2(1u, static_cast<uint32_t>(B));
+    w[1] = small_pair_f16x2(static_cast<uint32_t>(C), static_cast<uint32_t>(D));
+    w[2] = small_pair_f16x2(static_cast<uint32_t>(E), static_cast<uint32_t>(G));
+    w[3] = small_pair_f16x2(static_cast<uint32_t>(H), static_cast<uint32_t>(K));
     w[4] = half2_sub(__byte_perm(static_cast<uint32_t>(F), M, 0x4140), kH1024);
     w[5] = half2_sub(__byte_perm(static_cast<uint32_t>(I), M, 0x4140), kH1024);
     w[6] = half2_sub(__byte_perm(Alo, M, 0x4140), kH1024);
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
   uint8_t* dtiles = smem + P.stages * P.stage_bytes;
   unsigned long long* cta_acc = reinterpret_cast<unsigned long long*>(dtiles + kWarps * kDigitTileBytes);
   uint64_t* full = reinterpret_cast<uint64_t*>(cta_acc + kDigits * kDigits);
-  uint64_t* empty = full + 3;
+  uint64_t* empty = full + kExactMaxStages;
   __shared__ uint32_t s_bad;
   __shared__ uint32_t s_last;
 
@@ -444,7 +456,13 @@ int max_active(size_t smem) {
 
 size_t exact_smem_bytes(int stages, int stage_bytes) {
   return static_cast<size_t>(stages) * stage_bytes + kWarps * kDigitTileBytes +
-         kDigits * kDigits * sizeof(unsigned long long) + 6 * sizeof(uint64_t);
+         kDigits * kDigits * sizeof(unsigned long long) + 2 * kExactMaxStages * sizeof(uint64_t);
+}
+
+int exact_pick_stages(int stage_bytes) {
+  for (int st = kExactMaxStages; st >= 2; --st)
+    if (exact_smem_bytes(st, stage_bytes) <= 226 * 1024) return st;
+  return 0;
 }
 
 cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream) {
