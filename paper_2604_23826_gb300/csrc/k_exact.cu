@@ -312,13 +312,16 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
     // ---------------- producer: bulk copies of every column of each stage ----------------
     if (lane == 0 && !P.direct) {
       int64_t issued = 0;
-      for (int64_t k = 0; k < my_count; ++k) {
-        const int s = static_cast<int>(k % stages);
-        if (k >= stages && !mbar_wait_bounded(&empty[s], static_cast<uint32_t>((k / stages - 1) & 1))) {
+      int s = 0;
+      uint32_t ph = 0;  // phase parity of stage s's current use
+      int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTile;
+      const int64_t row_step = static_cast<int64_t>(gridDim.x) * kTile;
+      for (int64_t k = 0; k < my_count; ++k, row0 += row_step) {
+        // stage s was last used by tile k - stages, whose consumption completed phase ph ^ 1
+        if (k >= stages && !mbar_wait_bounded(&empty[s], ph ^ 1u)) {
           failed = 1;
           break;
         }
-        const int64_t row0 = (static_cast<int64_t>(blockIdx.x) + k * gridDim.x) * kTile;
         const uint32_t rows = static_cast<uint32_t>(min(static_cast<int64_t>(kTile), P.nmain - row0));
         uint32_t total = 0;
         for (int j = 0; j < P.p; ++j) total += rows * P.col_bytes[j];
@@ -328,6 +331,10 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
           bulk_g2s(dst + P.col_off[j], static_cast<const uint8_t*>(P.cols[j]) + row0 * P.col_bytes[j],
                    rows * P.col_bytes[j], &full[s]);
         issued = k + 1;
+        if (++s == stages) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
       // No copy may still be landing in shared memory when the block exits.
       for (int64_t k = max(static_cast<int64_t>(0), issued - stages); k < issued; ++k)
@@ -345,13 +352,15 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
       }
     const uint32_t tile = smem_u32(dtiles + warp * kDigitTileBytes);
     int sub = 0, flushes = 0;
-    for (int64_t k = 0; k < my_count; ++k) {
-      const int s = static_cast<int>(k % stages);
-      if (!P.direct && !mbar_wait_bounded(&full[s], static_cast<uint32_t>((k / stages) & 1))) {
+    int s = 0;
+    uint32_t ph = 0;  // phase parity of stage s's current use
+    int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTile;
+    const int64_t row_step = static_cast<int64_t>(gridDim.x) * kTile;
+    for (int64_t k = 0; k < my_count; ++k, row0 += row_step) {
+      if (!P.direct && !mbar_wait_bounded(&full[s], ph)) {
         failed = 1;
         break;
       }
-      const int64_t row0 = (static_cast<int64_t>(blockIdx.x) + k * gridDim.x) * kTile;
       const int valid = static_cast<int>(min(static_cast<int64_t>(kTile), P.nmain - row0));
       const uint8_t* st = stage_base + s * P.stage_bytes;
 #pragma unroll 1
@@ -379,6 +388,10 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
       }
       __syncwarp();
       if (lane == 0 && !P.direct) mbar_arrive(&empty[s]);
+      if (++s == stages) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
     // ragged tail (fewer than 8 rows), read from global memory by warp 0 of block 0
     if (blockIdx.x == 0 && warp == 0 && P.nrows > P.nmain) {
