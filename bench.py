@@ -25,6 +25,9 @@ import subprocess
 import sys
 import threading
 import time
+import math
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -61,6 +64,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
+    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256"), default="table1",
+                    help="table1: the headline line; tables4096 / wide256: the FP32 workloads")
+    ap.add_argument("--ntables", type=int, default=4096)
+    ap.add_argument("--wave-gb", type=float, default=64.0)
+    ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S")
     return ap.parse_args()
 
 
@@ -392,6 +400,211 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(out), flush=True)
     ctx.close()
 
+# ----------------------------------------------------------------------------- FP32 workloads
+MODE_NAMES = {"BF16X3": "STATS_BF16X3", "BF16X4": "STATS_BF16X4", "FP32": "STATS_FP32", "FP64S": "STATS_FP64_SHIFTED"}
+MODE_KERNEL = {"BF16X3": "split_kernel (mma.sync bf16)", "BF16X4": "split_kernel (mma.sync bf16)",
+               "FP32": "core_kernel<float>", "FP64S": "core_kernel<double>"}
+
+
+def _base_line(args, world, metric, value, ms_per_step, config, roofline, clocks, launches, extra):
+    out = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "roofline": roofline,
+           "e2e": None, "cpu_baseline": None, "gpu_launches": launches, "clocks": clocks}
+    out.update(extra)
+    return out
+
+
+def run_tables(args, rank: int, world: int, local_rank: int):
+    """Many independent FP32 tables (shapes of the batched workload), one batched call per wave."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+    from paper_2604_23826_gb300 import inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    seed = 3
+    mode_name = args.mode or "BF16X4"
+    mode = getattr(G, MODE_NAMES[mode_name])
+    params = inputs.many_tables_shapes(seed, args.ntables)
+    mine = list(range(rank, len(params), world))  # weak scaling: tables dealt round-robin to ranks
+    groups = inputs.waves([params[t] for t in mine], int(args.wave_gb * 1e9))
+    groups = [[mine[i] for i in g] for g in groups]
+    ctxs = {t: G.stats_init(G.Config([G.STATS_F32] * params[t][1], mode, [0] * params[t][1])) for t in mine}
+    rows_total = sum(params[t][0] for t in mine)
+    bytes_total = sum(4 * params[t][0] * params[t][1] for t in mine)
+    # each table is a [p, ld] block with ld = n rounded up to 4 floats: 16-byte aligned columns
+    ld = {t: (params[t][0] + 3) // 4 * 4 for t in mine}
+    buf = torch.empty(max(sum(params[t][1] * ld[t] for t in g) for g in groups), dtype=torch.float32, device=dev)
+
+    def materialise(g):
+        views, off = [], 0
+        for t in g:
+            n, p, mu, sd = params[t]
+            blk = buf[off:off + p * ld[t]].view(p, ld[t])
+            inputs.gen_table(torch, n, p, mu, sd, 1_000_003 * seed + t, dev, out=blk[:, :n])
+            views.append(blk[:, :n])
+            off += p * ld[t]
+        return views
+
+    wave_ms = []
+    # per wave: one pivot launch + one batched launch per tile width present (32: p <= 32, 64: p = 64)
+    launches_per_step = sum(1 + len({32 if params[t][1] <= 32 else 64 for t in g}) for g in groups)
+
+    def step(record: bool):
+        for t in mine:
+            G.stats_reset(ctxs[t])
+        total = 0.0
+        for g in groups:
+            views = materialise(g)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.stats_accumulate_batched([ctxs[t] for t in g], [[x[j] for j in range(x.shape[0])] for x in views],
+                                       [params[t][0] for t in g], stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        if record:
+            wave_ms.append(total)
+
+    for _ in range(args.warmup):
+        step(False)
+    sampler = ClockSampler(gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        step(True)
+    clocks = sampler.stop()
+    ms = sum(wave_ms) / len(wave_ms)
+    # finalize of every table once (reported, outside the pass time)
+    f0 = time.perf_counter()
+    worst_mean_rel = 0.0
+    for t in mine:
+        an = G.stats_finalize(ctxs[t])
+        n, p, mu, sd = params[t]
+        mu32, sd32 = np.float32(mu).astype(np.float64), np.float32(sd).astype(np.float64)
+        worst_mean_rel = max(worst_mean_rel, float(np.max(np.abs(an.mean - mu32) / sd32)) * math.sqrt(n))
+    fin_ms = (time.perf_counter() - f0) * 1e3
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    achieved = bytes_total / (ms / 1e3) / 1e9
+    t_ms = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    ms_all = t_ms.item()
+    rows_all = sum(params[t][0] for t in range(len(params)))
+    config = {"workload": f"tables{args.ntables}_seed{seed}_f32_{mode_name}", "tables": args.ntables,
+              "rows_total": rows_all, "bytes_total": sum(4 * n * p for n, p, _, _ in params),
+              "n_range": [1e3, 1e7], "p_choices": [8, 16, 32, 64], "mode": MODE_NAMES[mode_name],
+              "waves": len(groups), "wave_gb_max": args.wave_gb,
+              "step": "batched fused pass over every table (one launch per wave and tile size); "
+                      "inputs regenerated per wave outside the timed region",
+              "l2": "inputs larger than L2 (no flush)", "parallelism": f"tables dealt to {world} rank(s)"}
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "kernel": "gram32_kernel (register-fragment mma.sync bf16)" if mode_name.startswith("BF16")
+            else MODE_KERNEL[mode_name],
+            "kernel_ms": ms, "algorithmic_bytes": bytes_total}
+    extra = {"finalize_ms_all_tables": fin_ms,
+             "check_means_within_sqrt_n_sigma_units": worst_mean_rel}
+    out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, batched FP32 tables",
+                     rows_all / (ms_all / 1e3), ms_all, config, roof, clocks,
+                     launches_per_step * args.steps, extra)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for c in ctxs.values():
+        c.close()
+
+
+def run_wide(args, rank: int, world: int, local_rank: int):
+    """One wide correlated FP32 table (n x 256), timed in each FP32 mode."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+    from paper_2604_23826_gb300 import inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    seed, p = 4, 256
+    n = int(args.n) if args.n != 1e9 else 100_000_000
+    L, mu = inputs.wide_factor(seed, p)
+    X = inputs.gen_wide(torch, n, L, mu, seed * 1_000_003 + rank, dev)
+    torch.cuda.synchronize()
+    cols = [X[j] for j in range(p)]
+    modes = [args.mode] if args.mode else ["BF16X3", "BF16X4", "FP32", "FP64S"]
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    tflops = peaks.get("bf16_tflops")
+    results = {}
+    sampler = ClockSampler(gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    for mname in modes:
+        mode = getattr(G, MODE_NAMES[mname])
+        nm = n
+        steps = args.steps if mname != "FP64S" else 1  # the FP64 pass is FP64-FMA bound: one timed pass
+        cm = [c[:nm] for c in cols]
+        with G.stats_init(G.Config([G.STATS_F32] * p, mode, [0] * p)) as ctx:
+            if mname != "FP64S":
+                G.stats_accumulate(ctx, cm, nm, stream)
+                G.stats_sync(ctx)
+            ev = []
+            for _ in range(steps):
+                G.stats_reset(ctx)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                G.stats_accumulate(ctx, cm, nm, stream)
+                e1.record(stream)
+                ev.append((e0, e1))
+            an = G.stats_finalize(ctx)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        top = np.asarray(an.evals[:10])
+        results[mname] = {"rows": nm, "ms": ms, "rows_per_s": nm / (ms / 1e3),
+                          "GB_per_s": 4 * p * nm / (ms / 1e3) / 1e9,
+                          "hbm_frac": 4 * p * nm / (ms / 1e3) / 1e9 / peak,
+                          "top10_eval_rel_to_1_over_k": float(np.max(np.abs(top - 1.0 / np.arange(1, 11)) *
+                                                                     np.arange(1, 11))),
+                          "cov": an.cov}
+    clocks = sampler.stop()
+    ref = results.get("FP64S")
+    main_mode = modes[0]
+    for mname, r in results.items():
+        if ref is not None and mname != "FP64S" and r["rows"] == n and ref["rows"] == n:
+            r["cov_rel_vs_fp64s"] = float(np.linalg.norm(r["cov"] - ref["cov"]) / np.linalg.norm(ref["cov"]))
+    for r in results.values():
+        del r["cov"]
+    m = results[main_mode]
+    flops_row = {"BF16X3": 3, "BF16X4": 4}.get(main_mode, 1) * 2 * (p * (p + 1) // 2 + p)
+    config = {"workload": f"wide_n{n:.0e}_p{p}_seed{seed}_f32".replace("+", ""), "rows_per_gpu": n, "p": p,
+              "bytes_per_row": 4 * p, "mode": MODE_NAMES[main_mode], "modes_timed": modes,
+              "step": "one fused pass over the table", "l2": "inputs larger than L2 (no flush)",
+              "parallelism": f"rows sharded, {world} replica(s)"}
+    roof = {"bound": "hbm", "achieved": m["GB_per_s"], "peak": peak, "unit": "GB/s", "frac": m["hbm_frac"],
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "kernel": MODE_KERNEL[main_mode], "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
+            "tensor_tflops_useful": flops_row * n / (m["ms"] / 1e3) / 1e12, "tensor_peak_tflops": tflops}
+    t_ms = torch.tensor([m["ms"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, wide FP32 table",
+                     world * n / (t_ms.item() / 1e3), t_ms.item(), config, roof, clocks,
+                     2 * (args.steps if main_mode != "FP64S" else 1), {"modes": results})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
 
 def main():
     args = parse_args()
@@ -407,7 +620,12 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "tables4096":
+            run_tables(args, rank, world, local_rank)
+        elif args.workload == "wide256":
+            run_wide(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

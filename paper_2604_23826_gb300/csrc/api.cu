@@ -12,6 +12,8 @@
 #include <vector>
 
 #include "../../include/stats.h"
+#include <cuda.h>
+
 #include "kernels.h"
 
 using namespace ss;
@@ -259,6 +261,192 @@ stats_status ensure_slots(stats_ctx* c, int grid) {
   return STATS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 tables of up to 64 columns in BF16x3 / BF16x4 mode: register-fragment
+// tensor-core pass over a list of (table, row range) units.  The launch's
+// scratch (descriptors, unit list, tickets, unit and warp slots) lives in one
+// per-device workspace; launches that share it are ordered through an event.
+// ---------------------------------------------------------------------------
+struct Gram32Job {
+  stats_ctx* c;
+  const void* const* cols;
+  int64_t nrows;
+};
+
+struct Gram32Workspace {
+  void* dev = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t last = nullptr;
+};
+std::mutex g_g32_mu;
+Gram32Workspace g_g32_ws[64];
+
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// A 2D tensor map over p FP32 columns that sit a fixed, 16-byte-multiple stride apart
+// (column j at cols[0] + j * stride), box = rows x P columns; false when the columns
+// are not laid out that way or the map cannot be made.
+bool table_tensor_map(const void* const* cols, int p, int64_t nrows, int P, int rows, CUtensorMap* out) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || nrows <= 0 || nrows >= (int64_t(1) << 31) || !aligned16(cols[0])) return false;
+  const char* c0 = static_cast<const char*>(cols[0]);
+  int64_t stride = p > 1 ? static_cast<const char*>(cols[1]) - c0 : (nrows * 4 + 15) / 16 * 16;
+  if (stride <= 0 || stride % 16 != 0 || stride >= (int64_t(1) << 40)) return false;
+  for (int j = 2; j < p; ++j)
+    if (static_cast<const char*>(cols[j]) - c0 != j * stride) return false;
+  const cuuint64_t dim[2] = {static_cast<cuuint64_t>(nrows), static_cast<cuuint64_t>(p)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(rows), static_cast<cuuint32_t>(P)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<char*>(c0), dim, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
+  if (jobs.empty()) return STATS_OK;
+  stats_ctx* c0 = jobs[0].c;
+  int dev = 0;
+  CK(c0, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return STATS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_g32_mu);
+  Gram32Workspace& ws = g_g32_ws[dev];
+  if (!ws.last) CK(c0, cudaEventCreateWithFlags(&ws.last, cudaEventDisableTiming));
+  CK(c0, cudaStreamWaitEvent(st, ws.last, 0));  // the previous user of the workspace is done
+  const int sms = std::max(1, c0->sms);
+  // one launch per (P, x4) and per kGram32MaxTables tables
+  for (int P : {8, 16, 32, 64}) {
+    for (int x4 = 0; x4 < 2; ++x4) {
+      std::vector<const Gram32Job*> all;
+      for (const Gram32Job& j : jobs)
+        if (gram32_width(j.c->p) == P && (j.c->mode == STATS_BF16X4) == (x4 == 1) && j.nrows > 0) all.push_back(&j);
+      for (size_t first = 0; first < all.size(); first += kGram32MaxTables) {
+        const size_t nt = std::min<size_t>(kGram32MaxTables, all.size() - first);
+        const int64_t rs = gram32_rows_per_stage(P);
+        std::vector<Gram32Table> tabs(nt);
+        std::vector<CUtensorMap> maps;
+        std::vector<int> map_of(nt, -1);
+        std::vector<const float*> colptrs;
+        std::vector<int> need_shift;
+        int64_t total = 0;
+        for (size_t i = 0; i < nt; ++i) total += (all[first + i]->nrows + rs - 1) / rs;
+        if (total >= (int64_t(1) << 31)) return STATS_EINVAL;  // over 2^31 stages in one call
+        const int64_t K = kGram32Chunk;
+        const int grid = static_cast<int>(std::min<int64_t>((total + K - 1) / K, sms));
+        const size_t sf = gram32_slot_floats(P);
+        size_t slot_floats_total = 0;
+        int flush_kb = 2048 / 16;
+        int64_t stage0 = 0;
+        for (size_t i = 0; i < nt; ++i) {
+          const Gram32Job* j = all[first + i];
+          stats_ctx* c = j->c;
+          Gram32Table& T = tabs[i];
+          T = Gram32Table{};
+          T.p = c->p;
+          T.nrows = j->nrows;
+          const int64_t ns = (T.nrows + rs - 1) / rs;
+          T.stage0 = static_cast<int32_t>(stage0);
+          const int64_t nch = (stage0 + ns - 1) / K - stage0 / K + 1;  // chunks the table overlaps
+          T.nslots = static_cast<int32_t>(std::min<int64_t>(grid, nch));
+          stage0 += ns;
+          T.shift = c->d_fshift;
+          T.shift_d = c->d_shift;
+          T.acc_s = c->d_fs;
+          T.acc_s_lo = c->d_fs_lo;
+          T.acc_S = c->d_fS;
+          T.acc_S_lo = c->d_fS_lo;
+          T.acc_n = c->d_fn;
+          T.status = c->d_status;
+          T.aligned = 1;
+          for (int jj = 0; jj < c->p; ++jj) {
+            const float* ptr = static_cast<const float*>(j->cols[jj]);
+            colptrs.push_back(ptr);
+            if (!aligned16(ptr)) T.aligned = 0;
+          }
+          slot_floats_total += static_cast<size_t>(T.nslots) * sf;
+          if (P >= 32) {
+            CUtensorMap m;
+            if (table_tensor_map(j->cols, c->p, T.nrows, P, static_cast<int>(rs), &m)) {
+              map_of[i] = static_cast<int>(maps.size());
+              maps.push_back(m);
+            }
+          }
+          if (!c->shift_set) need_shift.push_back(static_cast<int>(i));
+          if (c->flush_rows > 0) flush_kb = std::min(flush_kb, std::max(1, c->flush_rows / 16));
+        }
+        const size_t off_maps = round256(nt * sizeof(Gram32Table));
+        const size_t off_cols = off_maps + round256(maps.size() * sizeof(CUtensorMap));
+        const size_t off_tick = off_cols + round256(colptrs.size() * sizeof(void*));
+        const size_t off_which = off_tick + round256(nt * sizeof(unsigned int));
+        const size_t off_slot = off_which + round256(need_shift.size() * sizeof(int));
+        const size_t off_wslot = off_slot + round256(slot_floats_total * sizeof(float));
+        const size_t need = off_wslot + round256(static_cast<size_t>(grid) * kGram32Warps * sf * sizeof(float));
+        if (ws.bytes < need) {
+          if (ws.dev) CK(c0, cudaFree(ws.dev));  // synchronises the device
+          ws.dev = nullptr;
+          ws.bytes = 0;
+          CK(c0, cudaMalloc(&ws.dev, need));
+          ws.bytes = need;
+        }
+        char* base = static_cast<char*>(ws.dev);
+        size_t cp = 0, so = 0;
+        for (size_t i = 0; i < nt; ++i) {
+          tabs[i].cols = reinterpret_cast<const float* const*>(base + off_cols) + cp;
+          tabs[i].ticket = reinterpret_cast<unsigned int*>(base + off_tick) + i;
+          tabs[i].slots = reinterpret_cast<float*>(base + off_slot) + so;
+          tabs[i].tmap = map_of[i] >= 0 ? base + off_maps + static_cast<size_t>(map_of[i]) * sizeof(CUtensorMap) : nullptr;
+          cp += tabs[i].p;
+          so += static_cast<size_t>(tabs[i].nslots) * sf;
+        }
+        CK(c0, cudaMemcpyAsync(base, tabs.data(), nt * sizeof(Gram32Table), cudaMemcpyHostToDevice, st));
+        CK(c0, cudaMemcpyAsync(base + off_cols, colptrs.data(), colptrs.size() * sizeof(void*),
+                               cudaMemcpyHostToDevice, st));
+        if (!maps.empty())
+          CK(c0, cudaMemcpyAsync(base + off_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                 cudaMemcpyHostToDevice, st));
+        CK(c0, cudaMemsetAsync(base + off_tick, 0, nt * sizeof(unsigned int), st));
+        if (!need_shift.empty()) {
+          CK(c0, cudaMemcpyAsync(base + off_which, need_shift.data(), need_shift.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+          CK(c0, launch_gram32_shift(reinterpret_cast<const Gram32Table*>(base),
+                                     reinterpret_cast<const int*>(base + off_which),
+                                     static_cast<int>(need_shift.size()), st));
+          for (int i : need_shift) all[first + i]->c->shift_set = true;
+        }
+        Gram32Launch L{};
+        L.tabs = reinterpret_cast<const Gram32Table*>(base);
+        L.warp_scratch = reinterpret_cast<float*>(base + off_wslot);
+        L.ntables = static_cast<int32_t>(nt);
+        L.total_stages = static_cast<int32_t>(total);
+        L.chunk = static_cast<int32_t>(K);
+        L.flush_kblocks = flush_kb;
+        CK(c0, launch_gram32(L, P, x4 == 1, grid, st));
+        for (size_t i = 0; i < nt; ++i) all[first + i]->c->last = st;
+      }
+    }
+  }
+  CK(c0, cudaEventRecord(ws.last, st));
+  return STATS_OK;
+}
+
 stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
   if (nrows == 0) return STATS_OK;
   const int grid = default_grid(c);
@@ -274,6 +462,10 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
     int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
     CK(c, launch_exact(P, c->conv, g, st));
+  } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64) {
+    std::vector<Gram32Job> jobs{{c, dcols, nrows}};
+    stats_status s = run_gram32(jobs, st);
+    if (s != STATS_OK) return s;
   } else if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
     SplitParams S{};
     for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
@@ -653,8 +845,10 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
                                       const int64_t* nrows, void* stream) {
   if (ntables < 0 || (ntables > 0 && (!ctxs || !dcols || !nrows))) return STATS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // tables not on the split path go one by one through stats_accumulate
+  // tables not on the split path go one by one through stats_accumulate; split tables of
+  // up to 64 columns share the register-fragment launch, wider ones the tiled launch
   std::vector<int> split_idx;
+  std::vector<Gram32Job> g32;
   for (int t = 0; t < ntables; ++t) {
     stats_ctx* c = ctxs[t];
     stats_status s = check_sticky(c);
@@ -664,11 +858,18 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
-      split_idx.push_back(t);
+      if (c->p <= 64)
+        g32.push_back({c, dcols[t], nrows[t]});
+      else
+        split_idx.push_back(t);
     } else {
       s = stats_accumulate(c, dcols[t], nrows[t], stream);
       if (s != STATS_OK) return s;
     }
+  }
+  if (!g32.empty()) {
+    stats_status s = run_gram32(g32, st);
+    if (s != STATS_OK) return s;
   }
   if (split_idx.empty()) return STATS_OK;
   int dev = 0;
@@ -684,6 +885,7 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
   std::vector<int64_t> unit_rows[2][2];
   const size_t off_cols = ((nt * sizeof(SplitParams) + 255) / 256) * 256;
   const size_t off_units = off_cols + ((ncolptr * sizeof(void*) + 255) / 256) * 256;
+  std::vector<int> need_shift;  // descriptors whose table gets its pivot in this call
   std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchWorkspace& ws = g_batch_ws[dev];
   size_t total_units = 0;
@@ -718,6 +920,8 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     S.acc_S = c->d_fS;
     S.acc_S_lo = c->d_fS_lo;
     S.acc_n = c->d_fn;
+    S.shift_d = c->d_shift;
+    if (!c->shift_set) need_shift.push_back(static_cast<int>(i));
     for (int j = 0; j < c->p; ++j) colptrs[cp + j] = static_cast<const float*>(dcols[t][j]);
     cp += c->p;
     const int a = T == 64 ? 1 : 0, b = c->mode == STATS_BF16X4 ? 1 : 0;
@@ -727,7 +931,8 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     }
     total_units += g;
   }
-  const size_t need = off_units + total_units * sizeof(int2) + 256;
+  const size_t off_which = off_units + ((total_units * sizeof(int2) + 255) / 256) * 256;
+  const size_t need = off_which + need_shift.size() * sizeof(int) + 256;
   if (ws.bytes < need) {
     if (ws.dev) CK(ctxs[split_idx[0]], cudaFree(ws.dev));
     ws.dev = nullptr;
@@ -760,16 +965,14 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
   CK(c0, cudaMemcpyAsync(base + off_cols, colptrs.data(), ncolptr * sizeof(void*), cudaMemcpyHostToDevice, st));
   CK(c0, cudaMemcpyAsync(base + off_units, all_units.data(), all_units.size() * sizeof(int2), cudaMemcpyHostToDevice,
                          st));
-  // pivots of tables seen for the first time
-  for (size_t i = 0; i < nt; ++i) {
-    stats_ctx* c = ctxs[split_idx[i]];
-    if (!c->shift_set) {
-      SplitParams S = descs[i];
-      S.col_ptrs = nullptr;
-      for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[split_idx[i]][j]);
-      CK(c, launch_split_shift(S, c->d_shift, st));
-      c->shift_set = true;
-    }
+  // pivots of tables seen for the first time: one launch for all of them
+  if (!need_shift.empty()) {
+    CK(c0, cudaMemcpyAsync(base + off_which, need_shift.data(), need_shift.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+    CK(c0, launch_split_shift_batched(reinterpret_cast<const SplitParams*>(base),
+                                      reinterpret_cast<const int*>(base + off_which),
+                                      static_cast<int>(need_shift.size()), st));
+    for (int i : need_shift) ctxs[split_idx[i]]->shift_set = true;
   }
   const SplitParams* dtabs = reinterpret_cast<const SplitParams*>(base);
   const int2* dunits = reinterpret_cast<const int2*>(base + off_units);

@@ -1,0 +1,604 @@
+// k_gram32.cu -- sufficient statistics of FP32 tables of up to 64 columns on the
+// tensor cores, register-fragment form of the bf16 split (BF16x3 / BF16x4):
+// arxiv 2604.23826, "Data Representation and Sufficient Statistics" (column sums
+// and X^T X in one streaming pass, partials over row ranges combined), with the
+// shift of "Numerical Considerations" (r = x - c, c = the table's first row, so
+// that X^T X and n mu mu^T are never formed separately).
+//
+// Each value becomes r = h + l, h = bf16(r), l = bf16(r - h), and
+//   S' = sum r r^T  ~  L^T H + H^T L + H^T H + diag(L^T L)   (BF16x3)
+//                    + L^T L                                (BF16x4, issued first).
+// The dropped L^T L is ~2^-16 of S'; its diagonal (sum of l^2 >= 0) is a bias that
+// does not average out, so BF16x3 adds it from the CUDA cores (an FFMA per value);
+// the off-diagonal terms are sums of products of rounding residuals and cancel.
+//
+// Data path.  The launch's tables are cut into 32 KB stages (8192 / P rows x P
+// columns); the stages of all tables, in order, are dealt round-robin to the
+// persistent CTAs (CTA b takes stages b, b + G, b + 2G, ...), so that at any
+// moment the CTAs read neighbouring row ranges of every column.  In a CTA a
+// producer warp streams its stages into a four-deep shared-memory ring with
+// one bulk copy (cp.async.bulk, mbarrier completion) per column; columns sit
+// RS + 16 floats apart, so that the consumers' 128-bit loads are free of bank
+// conflicts.  Seven consumer warps take the 16-row K blocks in turn.  Lane
+// (g, t) reads rows 4t..4t+3 of columns g + 8m with one 128-bit load per m;
+// those four rows fill the k slots (2t, 2t+1, 2t+8, 2t+9) of both the A
+// fragment (m16n8k16, A = X^T: rows = columns of X) and the B fragment
+// (B = X), so the operands never leave registers and no value is converted
+// twice.  Any assignment of rows to k slots gives the same X^T X, as long as A
+// and B use the same one.
+//
+// Accumulation.  The FP32 accumulation inside the tensor core truncates, with
+// an error that grows with the magnitude already held in the accumulator.
+// Every K block therefore starts a fresh MMA chain (C = 0, smallest products
+// first) whose 16-row result is added, rounding to nearest, into per-lane FP32
+// accumulators; every flush_kblocks K blocks of a warp those are added with
+// TwoSum into (hi, lo) pairs kept per warp in global scratch.  Column sums of r
+// come from the same registers.  When a CTA's run of stages in one table ends,
+// its consumer warps add their pairs, in warp order, into the CTA's slot of
+// that table; the CTA that completes a table's last slot adds the table's
+// slots, in slot order, into its double-double accumulators.  Every
+// floating-point addition has a fixed order given by the grid and the table
+// list: results do not depend on scheduling.
+//
+// A unit's ragged last K block is padded by the producer with the pivot (r = 0).
+// Tables whose columns are not all 16-byte aligned are staged by the producer
+// lanes with plain loads (correct, slower).  Every wait is bounded; on expiry
+// the CTA records STATS_ETIMEOUT in the table's status word, stops waiting,
+// lets its issued copies land and returns.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ss {
+
+namespace {
+
+constexpr int kGC = kGram32Warps;          // consumer warps
+constexpr int kGThreads = 32 * (kGC + 1);  // + one producer warp
+template <int P>
+struct G32 {
+  // P >= 32: 240-row stages, filled by one 2D tensor copy when the table's columns are
+  // uniformly strided (a 960-byte column stride is free of bank conflicts as it is);
+  // P <= 16: 32 KB stages of per-column bulk copies (2-4 KB each), columns RS + 16 apart
+  static constexpr bool TMAP = P >= 32;
+  static constexpr int STAGES = P == 64 ? 3 : P == 32 ? 6 : 4;
+  static constexpr int RS = TMAP ? 240 : 8192 / P;  // rows per stage
+  static constexpr int LDC = TMAP ? RS : RS + 16;   // column stride in floats (= 16 mod 32)
+  static constexpr int SF = P * LDC;                // floats per stage
+  static constexpr int KBS = RS / 16;         // K blocks per stage
+  static constexpr int NM = P / 8;            // column groups of a lane: columns g + 8m
+  static constexpr int NI = P >= 16 ? P / 16 : 1;
+  static constexpr int NJ = P / 8;
+  static constexpr int tiles() {
+    int n = 0;
+    for (int I = 0; I < NI; ++I) n += NJ - 2 * I;
+    return n;
+  }
+  static constexpr int TILES = tiles();
+  static constexpr int E = 4 * TILES + 2 * NM;  // accumulator words per lane: tiles, sums, sums of l^2
+};
+
+__device__ __forceinline__ float4 lds128(const float* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(smem_u32(p)));
+  return v;
+}
+
+// (lo, hi) -> bf16x2 with lo in the low half (the lower k index of a fragment pair)
+__device__ __forceinline__ uint32_t pack_bf16x2(float2 v) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v.y), "f"(v.x));
+  return d;
+}
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t v) {
+  return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xFFFF0000u));
+}
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
+// 2D tensor copy of a box (rows x columns of a column-major table) into shared memory
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// consumer warps only (named barrier 1)
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kGC) : "memory"); }
+
+// bounded wait that also gives up once another warp of the CTA has recorded a failure
+__device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, volatile unsigned int* dead) {
+  if (mbar_try_wait(bar, parity)) return true;
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
+    if (*dead) return false;
+  }
+  return false;
+}
+
+// A lane's fragments of one K block (m16n8k16): rows 4t, 4t+1 of column group m fill
+// the k slots (2t, 2t+1), rows 4t+2, 4t+3 the k slots (2t+8, 2t+9).  B of the 8-column
+// block J is the register pair (h[J][0], h[J][1]); A of the 16-column block I (rows g
+// and g + 8 = column groups 2I and 2I + 1) is the quad (h[2I][0], h[2I+1][0], h[2I][1],
+// h[2I+1][1]).
+template <int P>
+struct Frag {
+  uint32_t h[G32<P>::NM][2], l[G32<P>::NM][2];    // B pairs
+  uint32_t qh[G32<P>::NI][4], ql[G32<P>::NI][4];  // A quads
+};
+
+// Convert one 16-row K block of a stage into register fragments.
+template <int P, bool X4>
+__device__ __forceinline__ void convert_kblock(const float* __restrict__ st, int kb, int g, int t,
+                                               const float2* __restrict__ npiv, float2 (&sum)[G32<P>::NM],
+                                               float2 (&lsq)[G32<P>::NM], Frag<P>& F) {
+  using C = G32<P>;
+#pragma unroll
+  for (int m = 0; m < C::NM; ++m) {
+    const float4 v = lds128(st + (g + 8 * m) * C::LDC + 16 * kb + 4 * t);
+    const float2 np = npiv[g + 8 * m];  // (-c, -c) of this lane's column, shared memory
+    const float2 r01 = __fadd2_rn(make_float2(v.x, v.y), np);
+    const float2 r23 = __fadd2_rn(make_float2(v.z, v.w), np);
+    sum[m] = __fadd2_rn(sum[m], __fadd2_rn(r01, r23));
+    const uint32_t h01 = pack_bf16x2(r01), h23 = pack_bf16x2(r23);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    F.h[m][0] = h01;
+    F.h[m][1] = h23;
+    const float2 e01 = __ffma2_rn(unpack_bf16x2(h01), m1, r01);  // r - h, exact
+    const float2 e23 = __ffma2_rn(unpack_bf16x2(h23), m1, r23);
+    F.l[m][0] = pack_bf16x2(e01);
+    F.l[m][1] = pack_bf16x2(e23);
+    if (!X4) {  // BF16x3: the diagonal of L^T L on the CUDA cores
+      lsq[m] = __ffma2_rn(e01, e01, lsq[m]);
+      lsq[m] = __ffma2_rn(e23, e23, lsq[m]);
+    }
+  }
+  constexpr bool kTwo = C::NM > 1;  // P = 8: the second row group of A is empty
+#pragma unroll
+  for (int I = 0; I < C::NI; ++I) {
+    const int m0 = 2 * I, m1 = kTwo ? 2 * I + 1 : 0;
+    F.qh[I][0] = F.h[m0][0];
+    F.qh[I][1] = kTwo ? F.h[m1][0] : 0u;
+    F.qh[I][2] = F.h[m0][1];
+    F.qh[I][3] = kTwo ? F.h[m1][1] : 0u;
+    F.ql[I][0] = F.l[m0][0];
+    F.ql[I][1] = kTwo ? F.l[m1][0] : 0u;
+    F.ql[I][2] = F.l[m0][1];
+    F.ql[I][3] = kTwo ? F.l[m1][1] : 0u;
+  }
+}
+
+// D = A B + Z (Z a register quad of zeros: a fresh chain) and D += A B, m16n8k16 bf16 -> f32
+__device__ __forceinline__ void mma_z(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1,
+                                      const float (&z)[4]) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%12,%13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(z[0]), "f"(z[1]), "f"(z[2]),
+        "f"(z[3]));
+}
+__device__ __forceinline__ void mma_acc(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The K block's products on every upper tile (smallest first), added into the FP32
+// accumulators.
+template <int P, bool X4>
+__device__ __forceinline__ void mma_kblock(const Frag<P>& F, const float (&z)[4], float (&acc)[G32<P>::TILES][4]) {
+  using C = G32<P>;
+  int ti = 0;
+#pragma unroll
+  for (int I = 0; I < C::NI; ++I) {
+#pragma unroll
+    for (int J = 2 * I; J < C::NJ; ++J, ++ti) {
+      float d[4];
+      if (X4) {
+        mma_z(d, F.ql[I], F.l[J][0], F.l[J][1], z);
+        mma_acc(d, F.ql[I], F.h[J][0], F.h[J][1]);
+      } else {
+        mma_z(d, F.ql[I], F.h[J][0], F.h[J][1], z);
+      }
+      mma_acc(d, F.qh[I], F.l[J][0], F.l[J][1]);
+      mma_acc(d, F.qh[I], F.h[J][0], F.h[J][1]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[ti][k] += d[k];
+    }
+  }
+}
+
+template <int P, bool X4>
+__global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_constant__ Gram32Launch L) {
+  using C = G32<P>;
+  constexpr int RS = C::RS, LDC = C::LDC, SF = C::SF, NJ = C::NJ, E = C::E, TILES = C::TILES;
+  extern __shared__ __align__(128) float ring[];
+  __shared__ __align__(8) uint64_t bars[2 * C::STAGES];
+  __shared__ int s_rows[C::STAGES];
+  __shared__ int s_stage0[kGram32MaxTables + 1];  // first global stage of every table, then the total
+  __shared__ unsigned int s_last;
+  __shared__ volatile unsigned int s_dead;
+  __shared__ float2 s_npiv[P];  // (-c_j, -c_j) of the consumers' current table
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  for (int i = threadIdx.x; i < L.ntables; i += kGThreads) s_stage0[i] = L.tabs[i].stage0;
+  if (threadIdx.x == 0) {
+    s_stage0[L.ntables] = L.total_stages;
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kGC);
+    }
+    s_dead = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kGC) {
+    // ------------------------------------------------------------------ producer
+    // the stages of all tables in order, dealt in chunks of L.chunk stages round-robin
+    // to the CTAs: neighbouring CTAs read neighbouring row ranges of a large table,
+    // and a small table stays in one CTA
+    int s = 0;
+    uint32_t ph = 0;
+    int64_t issued = 0;
+    bool dead = false;
+    int ti = -1;
+    const Gram32Table* T = nullptr;
+    const float* c0 = nullptr;
+    const float* c1 = nullptr;
+    int slot_cols[C::STAGES];  // columns of a ring slot that may hold non-zero data
+#pragma unroll
+    for (int k = 0; k < C::STAGES; ++k) slot_cols[k] = P;
+    // this CTA's stages: chunks b, b + G, ... of L.chunk consecutive stages
+    for (int64_t ch = b, gs = static_cast<int64_t>(b) * L.chunk; gs < L.total_stages && !dead;
+         (++gs == (ch + 1) * L.chunk) ? (ch += G, gs = ch * L.chunk) : 0) {
+      if (ti < 0 || gs >= s_stage0[ti + 1]) {
+        do {
+          ++ti;
+        } while (gs >= s_stage0[ti + 1]);
+        T = &L.tabs[ti];
+        c0 = lane < T->p ? T->cols[lane] : nullptr;
+        c1 = lane + 32 < T->p ? T->cols[lane + 32] : nullptr;
+      }
+      const int p = T->p;
+      const int64_t row0 = static_cast<int64_t>(gs - s_stage0[ti]) * RS;
+      const int rows = static_cast<int>(min(static_cast<int64_t>(RS), T->nrows - row0));
+      if (issued >= C::STAGES && !wait_live(&empty[s], ph ^ 1u, &s_dead)) {
+        dead = true;
+        break;
+      }
+      float* st = ring + s * SF;
+      if (C::TMAP && T->tmap && rows == RS) {  // one tensor copy: all P columns, zeros past p
+        if (lane == 0) {
+          s_rows[s] = rows;
+          mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(RS * P * 4));
+          tma_load_2d(st, T->tmap, static_cast<int>(row0), 0, &full[s]);
+        }
+#pragma unroll
+        for (int k = 0; k < C::STAGES; ++k)
+          if (k == s) slot_cols[k] = p;
+        __syncwarp();
+        ++issued;
+        if (++s == C::STAGES) {
+          s = 0;
+          ph ^= 1u;
+        }
+        continue;
+      }
+      bool generic = false;
+      int sc = 0;
+#pragma unroll
+      for (int k = 0; k < C::STAGES; ++k)
+        if (k == s) sc = slot_cols[k];
+      if (sc > p) {  // columns p.. of this slot must read as zero
+        for (int i = p * LDC + 4 * lane; i < sc * LDC; i += 128)
+          *reinterpret_cast<float4*>(st + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+        generic = true;
+      }
+#pragma unroll
+      for (int k = 0; k < C::STAGES; ++k)
+        if (k == s) slot_cols[k] = p;
+      const int bulk = T->aligned ? (rows & ~3) : 0;
+      const int nr = rows - bulk;
+      if (nr > 0) {  // rows not moved by bulk copies: plain loads by the producer lanes
+        for (int idx = lane; idx < p * nr; idx += 32) {
+          const int c = idx / nr, r = bulk + idx % nr;
+          st[c * LDC + r] = __ldg(T->cols[c] + row0 + r);
+        }
+        generic = true;
+      }
+      const int pad = ((rows + 15) & ~15) - rows;
+      if (pad > 0) {  // rows past the table's end up to the K block boundary hold the pivot: r = 0
+        for (int idx = lane; idx < p * pad; idx += 32) {
+          const int c = idx / pad, r = rows + idx % pad;
+          st[c * LDC + r] = __ldg(T->shift + c);
+        }
+        generic = true;
+      }
+      if (generic) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        s_rows[s] = rows;
+        mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(bulk) * 4u * static_cast<uint32_t>(p));
+      }
+      __syncwarp();
+      if (bulk > 0) {
+        if (c0) bulk_g2s(st + lane * LDC, c0 + row0, static_cast<uint32_t>(bulk) * 4u, &full[s]);
+        if (c1) bulk_g2s(st + (lane + 32) * LDC, c1 + row0, static_cast<uint32_t>(bulk) * 4u, &full[s]);
+      }
+      ++issued;
+      if (++s == C::STAGES) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    if (dead) {
+      s_dead = 1;
+      if (lane == 0 && T) atomicOr(T->status, DEV_ETIMEOUT);
+    }
+    // no copy may be in flight when the CTA exits: wait for the last issued stages to land
+    for (int k = 0; k < C::STAGES && k < issued; ++k) {
+      int sk = s - 1 - k;
+      uint32_t pk = ph;
+      while (sk < 0) {
+        sk += C::STAGES;
+        pk ^= 1u;
+      }
+      mbar_wait_bounded(&full[sk], pk);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------------- consumers
+  const int g = lane >> 2, t = lane & 3;
+  float zq[4];  // a quad of zeros in registers: the C operand that starts each chain
+#pragma unroll
+  for (int i = 0; i < 4; ++i) asm volatile("mov.b32 %0, 0;" : "=f"(zq[i]));
+  float2* scratch = reinterpret_cast<float2*>(L.warp_scratch) +
+                    (static_cast<size_t>(b) * kGC + warp) * (E * 32);
+  int s = 0;
+  uint32_t ph = 0;
+  bool dead = false;
+  int ti = -1;
+  int64_t ch = b, gs = static_cast<int64_t>(b) * L.chunk;
+  while (gs < L.total_stages) {
+    // a run of this CTA's stages in one table
+    do {
+      ++ti;
+    } while (gs >= s_stage0[ti + 1]);
+    const Gram32Table& T = L.tabs[ti];
+    const int p = T.p;
+    for (int c = threadIdx.x; c < P; c += 32 * kGC) {
+      const float v = c < p ? -__ldg(T.shift + c) : 0.f;
+      s_npiv[c] = make_float2(v, v);
+    }
+    consumers_sync();
+    float acc[TILES][4];
+    float2 sum[C::NM], lsq[C::NM];
+#pragma unroll
+    for (int i = 0; i < TILES; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+#pragma unroll
+    for (int m = 0; m < C::NM; ++m) sum[m] = lsq[m] = make_float2(0.f, 0.f);
+    bool fresh = true;
+    int since = 0;
+
+    // FP32 accumulators -> this warp's (hi, lo) pairs; one tile at a time (the empty asm
+    // keeps the compiler from hoisting every pair's load ahead of the first add)
+    auto flush = [&]() {
+#pragma unroll
+      for (int i = 0; i < TILES; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float2* a = scratch + (4 * i + k) * 32 + lane;
+          float2 hl = fresh ? make_float2(0.f, 0.f) : __ldcg(a);
+          two_sum(hl.x, hl.y, acc[i][k]);
+          __stcg(a, hl);
+          acc[i][k] = 0.f;
+        }
+        asm volatile("" ::: "memory");
+      }
+#pragma unroll
+      for (int m = 0; m < C::NM; ++m) {
+        float2* a = scratch + (4 * TILES + m) * 32 + lane;
+        float2 hl = fresh ? make_float2(0.f, 0.f) : __ldcg(a);
+        two_sum(hl.x, hl.y, sum[m].x + sum[m].y);
+        __stcg(a, hl);
+        sum[m] = make_float2(0.f, 0.f);
+        float2* q = scratch + (4 * TILES + C::NM + m) * 32 + lane;
+        float2 ql = fresh ? make_float2(0.f, 0.f) : __ldcg(q);
+        two_sum(ql.x, ql.y, lsq[m].x + lsq[m].y);
+        __stcg(q, ql);
+        lsq[m] = make_float2(0.f, 0.f);
+      }
+      fresh = false;
+    };
+
+    int rot = 0;  // K blocks of this run before the current stage, mod kGC
+    const int end = s_stage0[ti + 1];
+    for (; gs < end && gs < L.total_stages; (++gs == (ch + 1) * L.chunk) ? (ch += G, gs = ch * L.chunk) : 0) {
+      if (!dead && !wait_live(&full[s], ph, &s_dead)) {
+        dead = true;
+        s_dead = 1;
+        if (lane == 0) atomicOr(T.status, DEV_ETIMEOUT);
+      }
+      if (!dead) {
+        const int rows = s_rows[s];
+        const float* st = ring + s * SF;
+        // K blocks kb0, kb0 + kGC, ...: the run's K block (stage * KBS + kb) = warp mod kGC
+        const int kb0 = (warp - rot + kGC) % kGC;
+        const int nkb = (rows + 15) >> 4;  // a ragged last K block is padded with the pivot
+        int done = 0;
+#pragma unroll 1
+        for (int kb = kb0; kb < nkb; kb += kGC, ++done) {
+          Frag<P> F;
+          convert_kblock<P, X4>(st, kb, g, t, s_npiv, sum, lsq, F);
+          mma_kblock<P, X4>(F, zq, acc);
+        }
+        since += done;
+        if (since >= L.flush_kblocks) {
+          since = 0;
+          flush();
+        }
+        rot = (rot + C::KBS) % kGC;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (++s == C::STAGES) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    flush();  // also writes the pairs of a warp that had no K block
+    consumers_sync();
+
+    // this CTA's slot of the table: the consumer warps' pairs, in warp order
+    const int sid = static_cast<int>(((b - s_stage0[ti] / L.chunk) % G + G) % G);
+    float2* cslot = reinterpret_cast<float2*>(T.slots) + static_cast<size_t>(sid) * (E * 32);
+    const float2* wbase = reinterpret_cast<const float2*>(L.warp_scratch) + static_cast<size_t>(b) * kGC * (E * 32);
+    for (int i = threadIdx.x; i < E * 32; i += 32 * kGC) {
+      float h = 0.f, l = 0.f;
+#pragma unroll
+      for (int w = 0; w < kGC; ++w) {
+        const float2 v = __ldcg(wbase + static_cast<size_t>(w) * (E * 32) + i);
+        two_sum(h, l, v.x);
+        two_sum(h, l, v.y);
+      }
+      __stcg(cslot + i, make_float2(h, l));
+    }
+    __threadfence();
+    consumers_sync();
+    if (threadIdx.x == 0) s_last = (atomicAdd(T.ticket, 1u) == static_cast<unsigned int>(T.nslots - 1)) ? 1u : 0u;
+    consumers_sync();
+    if (s_last && !s_dead) {
+      __threadfence();
+      // the table's last slot: every packed-upper entry and column sum, slots in order
+      const int Tn = p * (p + 1) / 2;
+      const float2* slots = reinterpret_cast<const float2*>(T.slots);
+      for (int e = threadIdx.x; e < Tn + p; e += 32 * kGC) {
+        float h = 0.f, l = 0.f;
+        if (e < Tn) {
+          int j = 0, rm = e;
+          while (rm >= p - j) {
+            rm -= p - j;
+            ++j;
+          }
+          const int k2 = j + rm;
+          const int I = P >= 16 ? j / 16 : 0, J = k2 / 8;
+          int tix = 0;
+          for (int i = 0; i < I; ++i) tix += NJ - 2 * i;
+          tix += J - 2 * I;
+          const int lr = j - 16 * I, lc = k2 - 8 * J;
+          const int ln = (lr & 7) * 4 + (lc >> 1);
+          const int w = 4 * tix + 2 * (lr >> 3) + (lc & 1);
+          for (int v = 0; v < T.nslots; ++v) {
+            const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + w * 32 + ln);
+            two_sum(h, l, x.x);
+            two_sum(h, l, x.y);
+          }
+          if (!X4 && j == k2) {  // BF16x3: + the diagonal of L^T L
+            const int wq = 4 * TILES + C::NM + (j >> 3), gq = j & 7;
+            for (int v = 0; v < T.nslots; ++v)
+              for (int tt = 0; tt < 4; ++tt) {
+                const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + wq * 32 + gq * 4 + tt);
+                two_sum(h, l, x.x);
+                two_sum(h, l, x.y);
+              }
+          }
+        } else {
+          const int c = e - Tn, m = c >> 3, gg = c & 7;
+          const int w = 4 * TILES + m;
+          for (int v = 0; v < T.nslots; ++v)
+            for (int tt = 0; tt < 4; ++tt) {
+              const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + w * 32 + gg * 4 + tt);
+              two_sum(h, l, x.x);
+              two_sum(h, l, x.y);
+            }
+        }
+        double* dh = e < Tn ? &T.acc_S[e] : &T.acc_s[e - Tn];
+        double* dl = e < Tn ? &T.acc_S_lo[e] : &T.acc_s_lo[e - Tn];
+        const double vv = static_cast<double>(h) + static_cast<double>(l);
+        const double sd = *dh + vv;
+        const double bp = sd - *dh;
+        *dl += (*dh - (sd - bp)) + (vv - bp);
+        *dh = sd;
+      }
+      if (threadIdx.x == 0) {
+        *T.acc_n += T.nrows;
+        *T.ticket = 0u;
+      }
+    }
+    consumers_sync();
+  }
+}
+
+template <int P, bool X4>
+cudaError_t launch_p(const Gram32Launch& L, int grid, cudaStream_t st) {
+  const int smem = G32<P>::STAGES * G32<P>::SF * 4;
+  cudaError_t e = cudaFuncSetAttribute(gram32_kernel<P, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  gram32_kernel<P, X4><<<grid, kGThreads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+__global__ void gram32_shift_kernel(const Gram32Table* __restrict__ tabs, const int* __restrict__ which) {
+  const Gram32Table& T = tabs[which[blockIdx.x]];
+  for (int j = threadIdx.x; j < T.p; j += blockDim.x) {
+    const float v = T.cols[j][0];
+    const_cast<float*>(T.shift)[j] = v;
+    T.shift_d[j] = static_cast<double>(v);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram32_shift(const Gram32Table* tabs, const int* which, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  gram32_shift_kernel<<<count, 64, 0, st>>>(tabs, which);
+  return cudaGetLastError();
+}
+
+int gram32_width(int p) { return p <= 8 ? 8 : p <= 16 ? 16 : p <= 32 ? 32 : 64; }
+
+size_t gram32_slot_floats(int P) {
+  int E = 0;
+  switch (P) {
+    case 8: E = G32<8>::E; break;
+    case 16: E = G32<16>::E; break;
+    case 32: E = G32<32>::E; break;
+    default: E = G32<64>::E; break;
+  }
+  return static_cast<size_t>(E) * 32 * 2;
+}
+
+int gram32_rows_per_stage(int P) {
+  switch (P) {
+    case 8: return G32<8>::RS;
+    case 16: return G32<16>::RS;
+    case 32: return G32<32>::RS;
+    default: return G32<64>::RS;
+  }
+}
+
+cudaError_t launch_gram32(const Gram32Launch& L, int P, bool x4, int grid, cudaStream_t st) {
+  if (L.total_stages <= 0) return cudaSuccess;
+  switch (P) {
+    case 8: return x4 ? launch_p<8, true>(L, grid, st) : launch_p<8, false>(L, grid, st);
+    case 16: return x4 ? launch_p<16, true>(L, grid, st) : launch_p<16, false>(L, grid, st);
+    case 32: return x4 ? launch_p<32, true>(L, grid, st) : launch_p<32, false>(L, grid, st);
+    default: return x4 ? launch_p<64, true>(L, grid, st) : launch_p<64, false>(L, grid, st);
+  }
+}
+
+}  // namespace ss

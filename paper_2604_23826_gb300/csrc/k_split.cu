@@ -307,6 +307,15 @@ __global__ void split_shift_kernel(const __grid_constant__ SplitParams P, double
   }
 }
 
+__global__ void split_shift_batched_kernel(const SplitParams* __restrict__ tabs, const int* __restrict__ which) {
+  const SplitParams& P = tabs[which[blockIdx.x]];
+  for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
+    const float v = P.col_ptrs[j][0];
+    const_cast<float*>(P.shift)[j] = v;
+    P.shift_d[j] = static_cast<double>(v);
+  }
+}
+
 }  // namespace
 
 size_t split_slot_floats(int grid) { return static_cast<size_t>(grid) * 4 * kSlotFloats; }
@@ -342,6 +351,12 @@ cudaError_t launch_split_batched(const SplitParams* tabs, const int2* units, int
     else
       split_batched_kernel<64, false><<<nunits, kThreads, 0, stream>>>(tabs, units);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_shift_batched(const SplitParams* tabs, const int* which, int count, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  split_shift_batched_kernel<<<count, 64, 0, stream>>>(tabs, which);
   return cudaGetLastError();
 }
 

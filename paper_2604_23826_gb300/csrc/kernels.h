@@ -108,14 +108,60 @@ struct SplitParams {
   double* acc_S;
   double* acc_S_lo;
   long long* acc_n;
+  double* shift_d;      // batched launches: p doubles (device), the pivot as double for finalize
 };
 size_t split_slot_floats(int grid);
 int split_tile(int p);  // T = 32 or 64
 cudaError_t launch_split(const SplitParams& P, int T, bool x4, int grid, cudaStream_t stream);
 cudaError_t launch_split_shift(const SplitParams& P, double* shift_d, cudaStream_t stream);
+// pivots of tabs[which[i]] for i < count, one block per table (batched launches)
+cudaError_t launch_split_shift_batched(const SplitParams* tabs, const int* which, int count, cudaStream_t stream);
 // units[i] = (index into tabs, local block of that table); all tables share T and the mode
 cudaError_t launch_split_batched(const SplitParams* tabs, const int2* units, int nunits, int T, bool x4,
                                  cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// FP32 tables of up to 64 columns, bf16 split on the tensor cores with register
+// fragments (k_gram32.cu).  One launch (one CTA per SM, persistent) takes a list
+// of units (row ranges of tables); every table's accumulators are updated by
+// the CTA that finishes its last unit.
+// ---------------------------------------------------------------------------
+constexpr int kGram32Warps = 7;         // consumer warps per CTA (plus one producer warp)
+constexpr int kGram32MaxTables = 4096;  // tables per launch
+struct Gram32Table {
+  const float* const* cols;  // device array of p column pointers
+  const float* shift;        // p pivots (device)
+  float* slots;              // nslots * gram32_slot_floats(P) floats of scratch
+  unsigned int* ticket;      // zero between launches
+  double* acc_s;             // ctx accumulators (shifted), double-double
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+  double* shift_d;           // p pivots as double (device), for finalize
+  unsigned int* status;      // the ctx's device status word (DEV_* bits)
+  const void* tmap;          // 2D tensor map of the columns (uniform stride), or null
+  int64_t nrows;
+  int32_t p;
+  int32_t stage0;            // the table's first stage in the launch's stage list
+  int32_t nslots;            // CTAs that take stages of the table: min(grid, chunks it overlaps)
+  int32_t aligned;           // every column pointer 16-byte aligned
+};
+struct Gram32Launch {
+  const Gram32Table* tabs;
+  float* warp_scratch;       // grid * kGram32Warps * gram32_slot_floats(P) floats
+  int32_t ntables;
+  int32_t total_stages;
+  int32_t chunk;             // consecutive stages dealt to one CTA (chunk c goes to CTA c % grid)
+  int32_t flush_kblocks;     // 16-row K blocks between FP32 -> (hi, lo) flushes
+};
+constexpr int kGram32Chunk = 8;
+int gram32_width(int p);                 // P = 8, 16, 32 or 64
+size_t gram32_slot_floats(int P);        // floats of one warp / unit slot
+int gram32_rows_per_stage(int P);
+cudaError_t launch_gram32(const Gram32Launch& L, int P, bool x4, int grid, cudaStream_t st);
+// pivots (first rows) of tabs[which[i]], i < count
+cudaError_t launch_gram32_shift(const Gram32Table* tabs, const int* which, int count, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // CUDA-core comparators for any width: FP64 (raw / shifted) and FP32-core.
