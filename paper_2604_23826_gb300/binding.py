@@ -221,16 +221,19 @@ def stats_accumulate_host(ctx: Ctx, hcols: Sequence, nrows: int, chunk_rows: int
 def stats_accumulate_batched(ctxs: Sequence[Ctx], dcols: Sequence[Sequence], nrows: Sequence[int], stream=None):
     """Add table t (dcols[t]: its device columns, nrows[t] rows) to ctxs[t], all in one pass."""
     L = load()
-    L.stats_accumulate_batched.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
-                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_void_p)),
-                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+    L.stats_accumulate_batched.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]
     L.stats_accumulate_batched.restype = ctypes.c_int
     n = len(ctxs)
-    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
-    arrays = [_ptr_array(cols) for cols in dcols]
-    outer = (ctypes.POINTER(ctypes.c_void_p) * n)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_void_p)) for a in arrays])
-    rows = (ctypes.c_int64 * n)(*nrows)
-    _check(L.stats_accumulate_batched(handles, n, outer, rows, _stream_handle(stream)), "stats_accumulate_batched")
+    handles = np.fromiter((c.handle.value for c in ctxs), dtype=np.uint64, count=n)
+    # one flat array of column pointers and, per table, the address of its first entry
+    flat = np.fromiter((_ptr(x) for cols in dcols for x in cols), dtype=np.uint64)
+    counts = np.fromiter((len(cols) for cols in dcols), dtype=np.int64, count=n)
+    starts = np.concatenate(([0], np.cumsum(counts)[:-1])) if n else np.zeros(0, np.int64)
+    outer = (flat.ctypes.data + 8 * starts).astype(np.uint64)
+    rows = np.asarray(nrows, dtype=np.int64)
+    _check(L.stats_accumulate_batched(handles.ctypes.data, n, outer.ctypes.data, rows.ctypes.data,
+                                      _stream_handle(stream)), "stats_accumulate_batched")
 
 
 def stats_merge(dst: Ctx, src: Ctx):

@@ -70,6 +70,12 @@ struct stats_ctx {
   unsigned int* d_split_ticket = nullptr;
   int split_grid = 0;
   int flush_rows = 0;                   // 0: by table width
+  // the last 2D tensor map made for this ctx's FP32 columns (reused while the layout is the same)
+  const void* tmap_base = nullptr;
+  int64_t tmap_stride = 0, tmap_rows = 0;
+  int tmap_box = 0;
+  bool tmap_ok = false;
+  alignas(64) CUtensorMap tmap{};
   bool shift_set = false;
   double* d_out = nullptr;              // finalize result
   double* d_work = nullptr;             // finalize scratch
@@ -349,11 +355,13 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
         int64_t total = 0;
         for (size_t i = 0; i < nt; ++i) total += (all[first + i]->nrows + rs - 1) / rs;
         if (total >= (int64_t(1) << 31)) return STATS_EINVAL;  // over 2^31 stages in one call
-        const int64_t K = kGram32Chunk;
+        // chunks as long as possible while every CTA still gets >= kGram32ChunksPerCta of them
+        // (long runs: few per-table partials; many chunks: balanced CTAs)
+        const int64_t K = std::max<int64_t>(kGram32Chunk, total / (int64_t(sms) * kGram32ChunksPerCta));
         const int grid = static_cast<int>(std::min<int64_t>((total + K - 1) / K, sms));
         const size_t sf = gram32_slot_floats(P);
         size_t slot_floats_total = 0;
-        int flush_kb = 2048 / 16;
+        int flush_kb = 16384 / 16;  // K blocks of a warp between FP32 -> (hi, lo) flushes
         int64_t stage0 = 0;
         for (size_t i = 0; i < nt; ++i) {
           const Gram32Job* j = all[first + i];
@@ -383,10 +391,26 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
           }
           slot_floats_total += static_cast<size_t>(T.nslots) * sf;
           if (P >= 32) {
-            CUtensorMap m;
-            if (table_tensor_map(j->cols, c->p, T.nrows, P, static_cast<int>(rs), &m)) {
+            const int64_t stride = c->p > 1 ? static_cast<const char*>(j->cols[1]) - static_cast<const char*>(j->cols[0]) : 0;
+            const bool same = c->tmap_base == j->cols[0] && c->tmap_stride == stride && c->tmap_rows == T.nrows &&
+                              c->tmap_box == static_cast<int>(rs);
+            bool ok = false;
+            if (same) {
+              // the cached map covers the same columns when they still sit one stride apart
+              ok = c->tmap_ok;
+              for (int jj = 2; ok && jj < c->p; ++jj)
+                if (static_cast<const char*>(j->cols[jj]) - static_cast<const char*>(j->cols[0]) != jj * stride) ok = false;
+            } else {
+              ok = table_tensor_map(j->cols, c->p, T.nrows, P, static_cast<int>(rs), &c->tmap);
+              c->tmap_base = j->cols[0];
+              c->tmap_stride = stride;
+              c->tmap_rows = T.nrows;
+              c->tmap_box = static_cast<int>(rs);
+              c->tmap_ok = ok;
+            }
+            if (ok) {
               map_of[i] = static_cast<int>(maps.size());
-              maps.push_back(m);
+              maps.push_back(c->tmap);
             }
           }
           if (!c->shift_set) need_shift.push_back(static_cast<int>(i));
@@ -394,8 +418,7 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
         }
         const size_t off_maps = round256(nt * sizeof(Gram32Table));
         const size_t off_cols = off_maps + round256(maps.size() * sizeof(CUtensorMap));
-        const size_t off_tick = off_cols + round256(colptrs.size() * sizeof(void*));
-        const size_t off_which = off_tick + round256(nt * sizeof(unsigned int));
+        const size_t off_which = off_cols + round256(colptrs.size() * sizeof(void*));
         const size_t off_slot = off_which + round256(need_shift.size() * sizeof(int));
         const size_t off_wslot = off_slot + round256(slot_floats_total * sizeof(float));
         const size_t need = off_wslot + round256(static_cast<size_t>(grid) * kGram32Warps * sf * sizeof(float));
@@ -410,7 +433,6 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
         size_t cp = 0, so = 0;
         for (size_t i = 0; i < nt; ++i) {
           tabs[i].cols = reinterpret_cast<const float* const*>(base + off_cols) + cp;
-          tabs[i].ticket = reinterpret_cast<unsigned int*>(base + off_tick) + i;
           tabs[i].slots = reinterpret_cast<float*>(base + off_slot) + so;
           tabs[i].tmap = map_of[i] >= 0 ? base + off_maps + static_cast<size_t>(map_of[i]) * sizeof(CUtensorMap) : nullptr;
           cp += tabs[i].p;
@@ -422,7 +444,6 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
         if (!maps.empty())
           CK(c0, cudaMemcpyAsync(base + off_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                                  cudaMemcpyHostToDevice, st));
-        CK(c0, cudaMemsetAsync(base + off_tick, 0, nt * sizeof(unsigned int), st));
         if (!need_shift.empty()) {
           CK(c0, cudaMemcpyAsync(base + off_which, need_shift.data(), need_shift.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, st));

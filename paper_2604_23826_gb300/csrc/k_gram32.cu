@@ -34,9 +34,9 @@
 // accumulators; every flush_kblocks K blocks of a warp those are added with
 // TwoSum into (hi, lo) pairs kept per warp in global scratch.  Column sums of r
 // come from the same registers.  When a CTA's run of stages in one table ends,
-// its consumer warps add their pairs, in warp order, into the CTA's slot of
-// that table; the CTA that completes a table's last slot adds the table's
-// slots, in slot order, into its double-double accumulators.  Every
+// its consumer warps add their partials, in warp order, through a shared buffer
+// into the CTA's slot of that table; a second, small kernel then adds every
+// table's slots, in slot order, into its double-double accumulators.  Every
 // floating-point addition has a fixed order given by the grid and the table
 // list: results do not depend on scheduling.
 //
@@ -45,6 +45,8 @@
 // lanes with plain loads (correct, slower).  Every wait is bounded; on expiry
 // the CTA records STATS_ETIMEOUT in the table's status word, stops waiting,
 // lets its issued copies land and returns.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -64,7 +66,8 @@ struct G32 {
   static constexpr int RS = TMAP ? 240 : 8192 / P;  // rows per stage
   static constexpr int LDC = TMAP ? RS : RS + 16;   // column stride in floats (= 16 mod 32)
   static constexpr int SF = P * LDC;                // floats per stage
-  static constexpr int KBS = RS / 16;         // K blocks per stage
+  static constexpr int KBS = RS / 16;
+  static constexpr int UNROLL = P <= 8 ? 4 : P <= 32 ? 2 : 1;  // independent K blocks in flight per warp         // K blocks per stage
   static constexpr int NM = P / 8;            // column groups of a lane: columns g + 8m
   static constexpr int NI = P >= 16 ? P / 16 : 1;
   static constexpr int NJ = P / 8;
@@ -109,6 +112,28 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, in
           "r"(smem_u32(smem_dst)),
       "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// (h, l) += the (hi, lo) pairs at word `off` of slots 0..n-1 (slot stride `stride` pairs), in
+// slot order; eight loads in flight at a time
+__device__ __forceinline__ void add_slots(const float2* __restrict__ slots, int n, int stride, int off, float& h,
+                                          float& l) {
+  int v = 0;
+  for (; v + 8 <= n; v += 8) {
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = __ldcg(slots + static_cast<size_t>(v + k) * stride + off);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      two_sum(h, l, x[k].x);
+      two_sum(h, l, x[k].y);
+    }
+  }
+  for (; v < n; ++v) {
+    const float2 x = __ldcg(slots + static_cast<size_t>(v) * stride + off);
+    two_sum(h, l, x.x);
+    two_sum(h, l, x.y);
+  }
 }
 
 // consumer warps only (named barrier 1)
@@ -225,7 +250,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
   __shared__ __align__(8) uint64_t bars[2 * C::STAGES];
   __shared__ int s_rows[C::STAGES];
   __shared__ int s_stage0[kGram32MaxTables + 1];  // first global stage of every table, then the total
-  __shared__ unsigned int s_last;
   __shared__ volatile unsigned int s_dead;
   __shared__ float2 s_npiv[P];  // (-c_j, -c_j) of the consumers' current table
   uint64_t* full = bars;
@@ -394,33 +418,35 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
     bool fresh = true;
     int since = 0;
 
-    // FP32 accumulators -> this warp's (hi, lo) pairs; one tile at a time (the empty asm
-    // keeps the compiler from hoisting every pair's load ahead of the first add)
+    // FP32 accumulators -> this warp's (hi, lo) pairs, eight words at a time (their loads in
+    // flight together; the empty asm stops the compiler from hoisting every load ahead)
     auto flush = [&]() {
+      constexpr int B = 8;
 #pragma unroll
-      for (int i = 0; i < TILES; ++i) {
+      for (int e0 = 0; e0 < E; e0 += B) {
+        float2 hl[B];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float2* a = scratch + (4 * i + k) * 32 + lane;
-          float2 hl = fresh ? make_float2(0.f, 0.f) : __ldcg(a);
-          two_sum(hl.x, hl.y, acc[i][k]);
-          __stcg(a, hl);
-          acc[i][k] = 0.f;
+        for (int k = 0; k < B; ++k)
+          if (e0 + k < E) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(scratch + (e0 + k) * 32 + lane);
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int e = e0 + k;
+          if (e >= E) continue;
+          float w;
+          if (e < 4 * TILES) {
+            w = acc[e / 4][e % 4];
+            acc[e / 4][e % 4] = 0.f;
+          } else if (e < 4 * TILES + C::NM) {
+            w = sum[e - 4 * TILES].x + sum[e - 4 * TILES].y;
+            sum[e - 4 * TILES] = make_float2(0.f, 0.f);
+          } else {
+            w = lsq[e - 4 * TILES - C::NM].x + lsq[e - 4 * TILES - C::NM].y;
+            lsq[e - 4 * TILES - C::NM] = make_float2(0.f, 0.f);
+          }
+          two_sum(hl[k].x, hl[k].y, w);
+          __stcg(scratch + e * 32 + lane, hl[k]);
         }
         asm volatile("" ::: "memory");
-      }
-#pragma unroll
-      for (int m = 0; m < C::NM; ++m) {
-        float2* a = scratch + (4 * TILES + m) * 32 + lane;
-        float2 hl = fresh ? make_float2(0.f, 0.f) : __ldcg(a);
-        two_sum(hl.x, hl.y, sum[m].x + sum[m].y);
-        __stcg(a, hl);
-        sum[m] = make_float2(0.f, 0.f);
-        float2* q = scratch + (4 * TILES + C::NM + m) * 32 + lane;
-        float2 ql = fresh ? make_float2(0.f, 0.f) : __ldcg(q);
-        two_sum(ql.x, ql.y, lsq[m].x + lsq[m].y);
-        __stcg(q, ql);
-        lsq[m] = make_float2(0.f, 0.f);
       }
       fresh = false;
     };
@@ -439,9 +465,18 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
         // K blocks kb0, kb0 + kGC, ...: the run's K block (stage * KBS + kb) = warp mod kGC
         const int kb0 = (warp - rot + kGC) % kGC;
         const int nkb = (rows + 15) >> 4;  // a ragged last K block is padded with the pivot
-        int done = 0;
+        int done = 0, kb = kb0;
+        constexpr int U = C::UNROLL;
 #pragma unroll 1
-        for (int kb = kb0; kb < nkb; kb += kGC, ++done) {
+        for (; kb + (U - 1) * kGC < nkb; kb += U * kGC, done += U) {
+          Frag<P> F[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) convert_kblock<P, X4>(st, kb + u * kGC, g, t, s_npiv, sum, lsq, F[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) mma_kblock<P, X4>(F[u], zq, acc);
+        }
+#pragma unroll 1
+        for (; kb < nkb; kb += kGC, ++done) {
           Frag<P> F;
           convert_kblock<P, X4>(st, kb, g, t, s_npiv, sum, lsq, F);
           mma_kblock<P, X4>(F, zq, acc);
@@ -460,95 +495,114 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
         ph ^= 1u;
       }
     }
-    flush();  // also writes the pairs of a warp that had no K block
-    consumers_sync();
-
-    // this CTA's slot of the table: the consumer warps' pairs, in warp order
-    const int sid = static_cast<int>(((b - s_stage0[ti] / L.chunk) % G + G) % G);
-    float2* cslot = reinterpret_cast<float2*>(T.slots) + static_cast<size_t>(sid) * (E * 32);
-    const float2* wbase = reinterpret_cast<const float2*>(L.warp_scratch) + static_cast<size_t>(b) * kGC * (E * 32);
-    for (int i = threadIdx.x; i < E * 32; i += 32 * kGC) {
-      float h = 0.f, l = 0.f;
+    // this CTA's slot of the table: the consumer warps' partials (FP32 accumulators plus,
+    // after mid-run flushes, the pairs in scratch) added in warp order through a shared
+    // buffer, one warp at a time (eight words per step, their loads issued together)
+    float2* __restrict__ red = reinterpret_cast<float2*>(ring + C::STAGES * SF) + lane;
+    for (int w = 0; w < kGC; ++w) {
+      if (warp == w) {
+        constexpr int B = 8;
 #pragma unroll
-      for (int w = 0; w < kGC; ++w) {
-        const float2 v = __ldcg(wbase + static_cast<size_t>(w) * (E * 32) + i);
-        two_sum(h, l, v.x);
-        two_sum(h, l, v.y);
-      }
-      __stcg(cslot + i, make_float2(h, l));
-    }
-    __threadfence();
-    consumers_sync();
-    if (threadIdx.x == 0) s_last = (atomicAdd(T.ticket, 1u) == static_cast<unsigned int>(T.nslots - 1)) ? 1u : 0u;
-    consumers_sync();
-    if (s_last && !s_dead) {
-      __threadfence();
-      // the table's last slot: every packed-upper entry and column sum, slots in order
-      const int Tn = p * (p + 1) / 2;
-      const float2* slots = reinterpret_cast<const float2*>(T.slots);
-      for (int e = threadIdx.x; e < Tn + p; e += 32 * kGC) {
-        float h = 0.f, l = 0.f;
-        if (e < Tn) {
-          int j = 0, rm = e;
-          while (rm >= p - j) {
-            rm -= p - j;
-            ++j;
-          }
-          const int k2 = j + rm;
-          const int I = P >= 16 ? j / 16 : 0, J = k2 / 8;
-          int tix = 0;
-          for (int i = 0; i < I; ++i) tix += NJ - 2 * i;
-          tix += J - 2 * I;
-          const int lr = j - 16 * I, lc = k2 - 8 * J;
-          const int ln = (lr & 7) * 4 + (lc >> 1);
-          const int w = 4 * tix + 2 * (lr >> 3) + (lc & 1);
-          for (int v = 0; v < T.nslots; ++v) {
-            const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + w * 32 + ln);
-            two_sum(h, l, x.x);
-            two_sum(h, l, x.y);
-          }
-          if (!X4 && j == k2) {  // BF16x3: + the diagonal of L^T L
-            const int wq = 4 * TILES + C::NM + (j >> 3), gq = j & 7;
-            for (int v = 0; v < T.nslots; ++v)
-              for (int tt = 0; tt < 4; ++tt) {
-                const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + wq * 32 + gq * 4 + tt);
-                two_sum(h, l, x.x);
-                two_sum(h, l, x.y);
+        for (int e0 = 0; e0 < E; e0 += B) {
+          float2 pr[B];
+#pragma unroll
+          for (int k = 0; k < B; ++k)
+            if (e0 + k < E) pr[k] = w == 0 ? make_float2(0.f, 0.f) : red[(e0 + k) * 32];
+          if (!fresh) {
+#pragma unroll
+            for (int k = 0; k < B; ++k)
+              if (e0 + k < E) {
+                const float2 q = __ldcg(scratch + (e0 + k) * 32 + lane);
+                two_sum(pr[k].x, pr[k].y, q.x);
+                two_sum(pr[k].x, pr[k].y, q.y);
               }
           }
-        } else {
-          const int c = e - Tn, m = c >> 3, gg = c & 7;
-          const int w = 4 * TILES + m;
-          for (int v = 0; v < T.nslots; ++v)
-            for (int tt = 0; tt < 4; ++tt) {
-              const float2 x = __ldcg(slots + static_cast<size_t>(v) * (E * 32) + w * 32 + gg * 4 + tt);
-              two_sum(h, l, x.x);
-              two_sum(h, l, x.y);
-            }
+#pragma unroll
+          for (int k = 0; k < B; ++k) {
+            const int e = e0 + k;
+            if (e >= E) continue;
+            float val;
+            if (e < 4 * TILES)
+              val = acc[e / 4][e % 4];
+            else if (e < 4 * TILES + C::NM)
+              val = sum[e - 4 * TILES].x + sum[e - 4 * TILES].y;
+            else
+              val = lsq[e - 4 * TILES - C::NM].x + lsq[e - 4 * TILES - C::NM].y;
+            two_sum(pr[k].x, pr[k].y, val);
+            red[e * 32] = pr[k];
+          }
         }
-        double* dh = e < Tn ? &T.acc_S[e] : &T.acc_s[e - Tn];
-        double* dl = e < Tn ? &T.acc_S_lo[e] : &T.acc_s_lo[e - Tn];
-        const double vv = static_cast<double>(h) + static_cast<double>(l);
-        const double sd = *dh + vv;
-        const double bp = sd - *dh;
-        *dl += (*dh - (sd - bp)) + (vv - bp);
-        *dh = sd;
       }
-      if (threadIdx.x == 0) {
-        *T.acc_n += T.nrows;
-        *T.ticket = 0u;
-      }
+      consumers_sync();
     }
-    consumers_sync();
+    const int sid = static_cast<int>(((b - s_stage0[ti] / L.chunk) % G + G) % G);
+    float2* cslot = reinterpret_cast<float2*>(T.slots) + static_cast<size_t>(sid) * (E * 32);
+    const float2* redb = reinterpret_cast<const float2*>(ring + C::STAGES * SF);
+    for (int i = threadIdx.x; i < E * 32; i += 32 * kGC) __stcg(cslot + i, redb[i]);
+    consumers_sync();  // the buffer is free for the next run
   }
+}
+
+// The tables' slots, in slot order, into their double-double accumulators: block
+// (t, part) takes every `parts`-th packed-upper entry and column sum of table t.
+template <int P, bool X4>
+__global__ void __launch_bounds__(256) gram32_merge_kernel(const Gram32Table* __restrict__ tabs, int parts) {
+  using C = G32<P>;
+  constexpr int E = C::E, TILES = C::TILES, NJ = C::NJ;
+  const Gram32Table& T = tabs[blockIdx.x / parts];
+  const int part = blockIdx.x % parts;
+  const int p = T.p;
+  const int Tn = p * (p + 1) / 2;
+  const float2* slots = reinterpret_cast<const float2*>(T.slots);
+  for (int e = part * 256 + threadIdx.x; e < Tn + p; e += parts * 256) {
+    float h = 0.f, l = 0.f;
+    if (e < Tn) {
+      int j = 0, rm = e;
+      while (rm >= p - j) {
+        rm -= p - j;
+        ++j;
+      }
+      const int k2 = j + rm;
+      const int I = P >= 16 ? j / 16 : 0, J = k2 / 8;
+      int tix = 0;
+      for (int i = 0; i < I; ++i) tix += NJ - 2 * i;
+      tix += J - 2 * I;
+      const int lr = j - 16 * I, lc = k2 - 8 * J;
+      const int ln = (lr & 7) * 4 + (lc >> 1);
+      const int w = 4 * tix + 2 * (lr >> 3) + (lc & 1);
+      add_slots(slots, T.nslots, E * 32, w * 32 + ln, h, l);
+      if (!X4 && j == k2) {  // BF16x3: + the diagonal of L^T L
+        const int wq = 4 * TILES + C::NM + (j >> 3), gq = j & 7;
+        for (int tt = 0; tt < 4; ++tt) add_slots(slots, T.nslots, E * 32, wq * 32 + gq * 4 + tt, h, l);
+      }
+    } else {
+      const int c = e - Tn, m = c >> 3, gg = c & 7;
+      const int w = 4 * TILES + m;
+      for (int tt = 0; tt < 4; ++tt) add_slots(slots, T.nslots, E * 32, w * 32 + gg * 4 + tt, h, l);
+    }
+    double* dh = e < Tn ? &T.acc_S[e] : &T.acc_s[e - Tn];
+    double* dl = e < Tn ? &T.acc_S_lo[e] : &T.acc_s_lo[e - Tn];
+    const double vv = static_cast<double>(h) + static_cast<double>(l);
+    const double sd = *dh + vv;
+    const double bp = sd - *dh;
+    *dl += (*dh - (sd - bp)) + (vv - bp);
+    *dh = sd;
+  }
+  if (part == 0 && threadIdx.x == 0) *T.acc_n += T.nrows;
 }
 
 template <int P, bool X4>
 cudaError_t launch_p(const Gram32Launch& L, int grid, cudaStream_t st) {
-  const int smem = G32<P>::STAGES * G32<P>::SF * 4;
+  const int smem = G32<P>::STAGES * G32<P>::SF * 4 + G32<P>::E * 32 * 8;  // ring + reduction buffer
   cudaError_t e = cudaFuncSetAttribute(gram32_kernel<P, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   gram32_kernel<P, X4><<<grid, kGThreads, smem, st>>>(L);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // merge: entries of a table spread over `parts` blocks, at least ~2 blocks per SM in all
+  const int entries = P * (P + 1) / 2 + P;
+  const int parts = std::max(1, std::min((entries + 255) / 256, (2 * grid + L.ntables - 1) / L.ntables));
+  gram32_merge_kernel<P, X4><<<L.ntables * parts, 256, 0, st>>>(L.tabs, parts);
   return cudaGetLastError();
 }
 

@@ -122,9 +122,9 @@ cudaError_t launch_split_batched(const SplitParams* tabs, const int2* units, int
 
 // ---------------------------------------------------------------------------
 // FP32 tables of up to 64 columns, bf16 split on the tensor cores with register
-// fragments (k_gram32.cu).  One launch (one CTA per SM, persistent) takes a list
-// of units (row ranges of tables); every table's accumulators are updated by
-// the CTA that finishes its last unit.
+// fragments (k_gram32.cu).  One launch (one CTA per SM, persistent) streams the
+// stages of a list of tables; a small second launch adds each table's per-CTA
+// slots, in slot order, into its accumulators.
 // ---------------------------------------------------------------------------
 constexpr int kGram32Warps = 7;         // consumer warps per CTA (plus one producer warp)
 constexpr int kGram32MaxTables = 4096;  // tables per launch
@@ -132,7 +132,6 @@ struct Gram32Table {
   const float* const* cols;  // device array of p column pointers
   const float* shift;        // p pivots (device)
   float* slots;              // nslots * gram32_slot_floats(P) floats of scratch
-  unsigned int* ticket;      // zero between launches
   double* acc_s;             // ctx accumulators (shifted), double-double
   double* acc_s_lo;
   double* acc_S;
@@ -155,7 +154,8 @@ struct Gram32Launch {
   int32_t chunk;             // consecutive stages dealt to one CTA (chunk c goes to CTA c % grid)
   int32_t flush_kblocks;     // 16-row K blocks between FP32 -> (hi, lo) flushes
 };
-constexpr int kGram32Chunk = 8;
+constexpr int kGram32Chunk = 32;         // smallest chunk (stages)
+constexpr int kGram32ChunksPerCta = 32;  // chunks a CTA gets at least, when the launch is large enough
 int gram32_width(int p);                 // P = 8, 16, 32 or 64
 size_t gram32_slot_floats(int P);        // floats of one warp / unit slot
 int gram32_rows_per_stage(int P);
