@@ -64,8 +64,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
-    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256"), default="table1",
-                    help="table1: the headline line; tables4096 / wide256: the FP32 workloads")
+    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table"), default="table1",
+                    help="table1: the headline line; tables4096 / wide256 / f32table: the FP32 workloads")
+    ap.add_argument("--p", type=int, default=64, help="f32table: columns")
     ap.add_argument("--ntables", type=int, default=4096)
     ap.add_argument("--wave-gb", type=float, default=64.0)
     ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S")
@@ -613,6 +614,69 @@ def run_wide(args, rank: int, world: int, local_rank: int):
         print(json.dumps(out), flush=True)
 
 
+def run_f32table(args, rank: int, world: int, local_rank: int):
+    """One FP32 table of the many-tables distribution (independent N(mu_j, sigma_j^2) columns), p columns,
+    n rows, stored as a [p, ld] block (ld = n rounded up to 4 floats), timed in one mode."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+    from paper_2604_23826_gb300 import inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    seed, p = 3, args.p
+    n = int(args.n) if args.n != 1e9 else int(16e9 / (4 * p))
+    mode_name = args.mode or "BF16X4"
+    rng = np.random.default_rng(seed)
+    mu, sd = rng.uniform(1e3, 1e5, p), rng.uniform(0.1, 10.0, p)
+    ld = (n + 3) // 4 * 4
+    blk = torch.empty((p, ld), dtype=torch.float32, device=dev)
+    X = inputs.gen_table(torch, n, p, mu, sd, seed * 1_000_003 + rank, dev, out=blk[:, :n])
+    cols = [X[j] for j in range(p)]
+    with G.stats_init(G.Config([G.STATS_F32] * p, getattr(G, MODE_NAMES[mode_name]), [0] * p)) as ctx:
+        for _ in range(args.warmup):
+            G.stats_reset(ctx)
+            G.stats_accumulate(ctx, cols, n, stream)
+        G.stats_sync(ctx)
+        sampler = ClockSampler(gpu_index(local_rank))
+        sampler.start()
+        time.sleep(0.3)
+        ev = []
+        for _ in range(args.steps):
+            G.stats_reset(ctx)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.stats_accumulate(ctx, cols, n, stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        an = G.stats_finalize(ctx)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs") or 6800.0
+    gbs = 4 * p * n / (ms / 1e3) / 1e9
+    mu32, sd32 = np.float32(mu).astype(np.float64), np.float32(sd).astype(np.float64)
+    config = {"workload": f"f32table_p{p}_n{n}_seed{seed}", "rows_per_gpu": n, "p": p, "bytes_per_row": 4 * p,
+              "mode": MODE_NAMES[mode_name], "layout": "[p, ld] block, ld = n rounded up to 4",
+              "step": "one fused pass over the table", "l2": "inputs larger than L2 (no flush)",
+              "parallelism": f"rows sharded, {world} replica(s)"}
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "kernel": "gram32_kernel (register-fragment mma.sync bf16)" if p <= 64 and mode_name.startswith("BF16")
+            else MODE_KERNEL[mode_name], "kernel_ms": ms, "algorithmic_bytes": 4 * p * n}
+    extra = {"check_means_within_sqrt_n_sigma_units": float(np.max(np.abs(an.mean - mu32) / sd32)) * math.sqrt(n)}
+    out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, one FP32 table",
+                     world * n / (ms / 1e3), ms, config, roof, clocks,
+                     (3 if p <= 64 and mode_name.startswith("BF16") else 2) * args.steps, extra)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -631,6 +695,8 @@ def main():
             run_tables(args, rank, world, local_rank)
         elif args.workload == "wide256":
             run_wide(args, rank, world, local_rank)
+        elif args.workload == "f32table":
+            run_f32table(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:
