@@ -70,8 +70,10 @@ typedef enum { STATS_I16 = 0, STATS_I32 = 1, STATS_I64 = 2, STATS_F32 = 3, STATS
  *                      row-parallel kernel for p <= 12, a tiled one above.
  *   STATS_FP64_SHIFTED FP64 CUDA cores on x - c, c = the first row accumulated.
  *   STATS_BF16X3       FP32 data: x - c split into bf16 h + l; S ~ H^T H + H^T L + L^T H
- *                      on tensor cores, FP32 accumulation flushed to FP64.
- *   STATS_BF16X4       as BF16X3 plus L^T L.
+ *                      on tensor cores (each 16-row block a fresh FP32 chain, added in
+ *                      round-to-nearest FP32, then double-double); for p <= 64 plus the
+ *                      diagonal of L^T L from the CUDA cores (its missing positive bias).
+ *   STATS_BF16X4       as BF16X3 plus all of L^T L on the tensor cores.
  *   STATS_FP32         FP32 CUDA-core FMA on x - c, flushed into FP32 (hi, lo) pairs.
  * The BF16 modes take FP32 columns only; the others take any dtype.             */
 typedef enum {
@@ -146,21 +148,30 @@ stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int
 
 /* Many independent tables in one pass: table t (ctx ctxs[t], nrows[t] rows, dcols[t]
  * a host array of ctxs[t]'s p device column pointers) is added to ctxs[t].  Tables
- * of STATS_BF16X3 / STATS_BF16X4 contexts run together in one persistent launch per
- * tile width (32 or 64 columns) and mode, each block taking one (table, tile, row
- * range) unit from a device-side work list, larger units first; other contexts go
- * through stats_accumulate one by one.  The descriptors are copied to a per-device
- * workspace inside the library (grown on demand), so batched calls must be issued
- * on one stream at a time.  A context appears at most once per call.
+ * of STATS_BF16X3 / STATS_BF16X4 contexts with p <= 64 run together in one
+ * persistent launch per padded width (8, 16, 32, 64) and mode (up to 4096 tables per
+ * launch): their 32-64 KB stages are dealt in chunks to one CTA per SM, and a second
+ * small launch adds each table's per-CTA partials in a fixed order (results depend
+ * only on the call, not on scheduling).  Tables whose columns sit one 16-byte-multiple
+ * stride apart (a [p, ld] block) are read with 2D tensor copies, others with one bulk
+ * copy per column.  Wider split tables use the tiled launch; contexts in other modes
+ * go through stats_accumulate one by one.  The descriptors go to a per-device
+ * workspace inside the library (grown on demand; use from one stream at a time).  A
+ * context appears at most once per call.
  * Errors: as stats_accumulate. */
 stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, const void* const* const* dcols,
                                       const int64_t* nrows, void* stream);
 
-/* dst += src, entry by entry, for two ctxs with identical configuration: the
- * combination of partial results from disjoint row subsets that the paper does
- * across its GPUs.  Exact for STATS_EXACT; FP64 modes add in double-double.
- * Enqueued on dst's last stream; src must be idle.  Errors: EINVAL (configs
- * differ), ESTATE. */
+/* dst += src for two ctxs with identical configuration: the combination of
+ * partial results from disjoint row subsets that the paper does across its GPUs
+ * ("Data Representation and Sufficient Statistics").  Exact for STATS_EXACT;
+ * STATS_FP64 adds in double-double.  The shifted modes (STATS_FP64_SHIFTED,
+ * STATS_BF16X3, STATS_BF16X4, STATS_FP32) hold moments about each ctx's own pivot
+ * (its first row): src's are re-expressed about dst's pivot, in double-double,
+ *   sum (x - c_d) = s'_src + n_src d,
+ *   sum (x - c_d)(x - c_d)^T = S'_src + d s'_src^T + s'_src d^T + n_src d d^T,
+ * with d = c_src - c_dst; an empty dst takes src's pivot.  Enqueued on dst's last
+ * stream; src must be idle.  Errors: EINVAL (configs differ), ESTATE. */
 stats_status stats_merge(stats_ctx* dst, const stats_ctx* src);
 
 /* Wait for all work of ctx and return its sticky device status. */
@@ -220,10 +231,12 @@ int32_t stats_num_analysis_columns(const stats_ctx* ctx);
  * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
 
-/* Tuning knob of STATS_BF16X3 / STATS_BF16X4: rows a warp accumulates in the
- * tensor cores' FP32 accumulators before adding them into its (hi, lo) pairs
- * (16..4096, a multiple of 16; default 16 for p <= 64, else 64).  The FP32
- * accumulation error grows about linearly with this interval.  Errors: EINVAL. */
+/* Tuning knob of STATS_BF16X3 / STATS_BF16X4 (16..4096, a multiple of 16).  For
+ * p > 64: rows a warp accumulates in the tensor cores' FP32 accumulators before
+ * adding them into its (hi, lo) pairs (default 64; the error grows about linearly
+ * with it).  For p <= 64 every 16 rows are a fresh tensor chain whatever the knob;
+ * it caps the rows of round-to-nearest FP32 accumulation before the (hi, lo) pairs
+ * (default 16384).  Errors: EINVAL. */
 stats_status stats_set_flush_rows(stats_ctx* ctx, int32_t rows);
 
 /* ---------------------------------------------------------------------------

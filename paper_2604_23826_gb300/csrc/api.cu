@@ -1018,9 +1018,8 @@ stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
           dst->plan[j].shift != src->plan[j].shift || dst->plan[j].is_signed != src->plan[j].is_signed)
         return STATS_EINVAL;
   }
-  if (dst->mode == STATS_FP64_SHIFTED || dst->mode == STATS_BF16X3 || dst->mode == STATS_BF16X4 ||
-      dst->mode == STATS_FP32)
-    return STATS_EINVAL;  // the pivots of two ctxs generally differ
+  const bool shifted = dst->mode == STATS_FP64_SHIFTED || dst->mode == STATS_BF16X3 || dst->mode == STATS_BF16X4 ||
+                       dst->mode == STATS_FP32;
   if (src->last) CK(dst, cudaStreamSynchronize(src->last));
   stats_ctx* srcm = const_cast<stats_ctx*>(src);
   // carry src's device error bits over
@@ -1033,6 +1032,20 @@ stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
     CK(dst, cudaMemcpy(dst->d_status, &mine, sizeof(mine), cudaMemcpyHostToDevice));
   }
   cudaStream_t st = dst->last;
+  if (shifted && !src->shift_set) return STATS_OK;  // src holds no rows
+  if (shifted && dst->shift_set) {
+    // the two ctxs generally have different pivots: re-express src about dst's pivot
+    CK(dst, launch_merge_shifted(dst->d_fs, dst->d_fs_lo, dst->d_fS, dst->d_fS_lo, dst->d_shift, src->d_fs,
+                                 src->d_fs_lo, src->d_fS, src->d_fS_lo, src->d_shift, src->d_fn, dst->p, st));
+    CK(dst, launch_merge_i64(dst->d_fn, src->d_fn, 1, st));
+    return STATS_OK;
+  }
+  if (shifted) {  // dst holds no rows yet: take src's pivot
+    CK(dst, cudaMemcpyAsync(dst->d_shift, src->d_shift, dst->p * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (dst->d_fshift && src->d_fshift)
+      CK(dst, cudaMemcpyAsync(dst->d_fshift, src->d_fshift, dst->p * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    dst->shift_set = true;
+  }
   if (dst->mode == STATS_EXACT) {
     CK(dst, launch_merge_i64(dst->d_g, src->d_g, kDigits * kDigits, st));
   } else {
@@ -1197,6 +1210,14 @@ stats_status stats_import(stats_ctx** out, const void* buf, size_t len) {
     return STATS_ECUDA;
   }
   c->shift_set = ss != 0;
+  if (c->shift_set && c->d_fshift) {  // the split kernels' float copy of the pivot
+    e = launch_pivot_to_float(c->d_shift, c->d_fshift, p, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      stats_destroy(c);
+      return STATS_ECUDA;
+    }
+  }
   *out = c;
   return STATS_OK;
 }

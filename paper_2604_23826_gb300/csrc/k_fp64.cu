@@ -157,6 +157,82 @@ __global__ void merge_dd_kernel(double* hi, double* lo, const double* shi, const
 }
 }  // namespace
 
+// dd helpers for the pivot change
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double bhi, double blo) {
+  double s, e;
+  two_sum(hi, bhi, s, e);
+  e += lo + blo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+__device__ __forceinline__ void dd_mul(double ahi, double alo, double bhi, double blo, double& hi, double& lo) {
+  const double p = ahi * bhi;
+  const double e = fma(ahi, bhi, -p) + (ahi * blo + alo * bhi);
+  hi = p + e;
+  lo = e - (hi - p);
+}
+
+// Shifted moments about pivot c_s (n_s rows: s' = sum (x - c_s), S' = sum (x - c_s)(x - c_s)^T)
+// re-expressed about c_d and added to the destination's: with d = c_s - c_d,
+//   sum (x - c_d)              = s' + n_s d
+//   sum (x - c_d)(x - c_d)^T   = S' + d s'^T + s' d^T + n_s d d^T      (packed upper)
+// in double-double (Chan, Golub and LeVeque's pairwise update with the two means replaced by pivots).
+__global__ void merge_shifted_kernel(double* s, double* s_lo, double* S, double* S_lo, const double* c_d,
+                                     const double* ss, const double* ss_lo, const double* Ss, const double* Ss_lo,
+                                     const double* c_s, const long long* n_s, int p) {
+  const int T = p * (p + 1) / 2;
+  const double ns = static_cast<double>(*n_s);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T + p; e += gridDim.x * blockDim.x) {
+    if (e < T) {
+      int j = 0, rm = e;
+      while (rm >= p - j) {
+        rm -= p - j;
+        ++j;
+      }
+      const int k = j + rm;
+      double dj, dj_lo, dk, dk_lo;
+      two_sum(c_s[j], -c_d[j], dj, dj_lo);
+      two_sum(c_s[k], -c_d[k], dk, dk_lo);
+      double hi = Ss[e], lo = Ss_lo[e], th, tl;
+      dd_mul(dj, dj_lo, ss[k], ss_lo[k], th, tl);
+      dd_add(hi, lo, th, tl);
+      dd_mul(dk, dk_lo, ss[j], ss_lo[j], th, tl);
+      dd_add(hi, lo, th, tl);
+      double dd_hi, dd_lo;
+      dd_mul(dj, dj_lo, dk, dk_lo, dd_hi, dd_lo);
+      dd_mul(dd_hi, dd_lo, ns, 0.0, th, tl);
+      dd_add(hi, lo, th, tl);
+      dd_add(S[e], S_lo[e], hi, lo);
+    } else {
+      const int j = e - T;
+      double dj, dj_lo, th, tl;
+      two_sum(c_s[j], -c_d[j], dj, dj_lo);
+      double hi = ss[j], lo = ss_lo[j];
+      dd_mul(dj, dj_lo, ns, 0.0, th, tl);
+      dd_add(hi, lo, th, tl);
+      dd_add(s[j], s_lo[j], hi, lo);
+    }
+  }
+}
+
+__global__ void pivot_to_float_kernel(const double* src, float* dst, int p) {
+  for (int j = threadIdx.x; j < p; j += blockDim.x) dst[j] = static_cast<float>(src[j]);
+}
+
+cudaError_t launch_pivot_to_float(const double* src, float* dst, int p, cudaStream_t stream) {
+  pivot_to_float_kernel<<<1, 256, 0, stream>>>(src, dst, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_shifted(double* s, double* s_lo, double* S, double* S_lo, const double* c_d,
+                                 const double* ss, const double* ss_lo, const double* Ss, const double* Ss_lo,
+                                 const double* c_s, const long long* n_s, int p, cudaStream_t stream) {
+  const int count = p * (p + 1) / 2 + p;
+  merge_shifted_kernel<<<(count + 255) / 256, 256, 0, stream>>>(s, s_lo, S, S_lo, c_d, ss, ss_lo, Ss, Ss_lo, c_s,
+                                                                 n_s, p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_merge_i64(long long* dst, const long long* src, int count, cudaStream_t stream) {
   merge_i64_kernel<<<(count + 255) / 256, 256, 0, stream>>>(dst, src, count);
   return cudaGetLastError();

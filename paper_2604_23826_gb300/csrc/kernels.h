@@ -248,5 +248,11 @@ cudaError_t launch_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int l
 cudaError_t launch_merge_i64(long long* dst, const long long* src, int count, cudaStream_t stream);
 cudaError_t launch_merge_dd(double* dst_hi, double* dst_lo, const double* src_hi, const double* src_lo, int count,
                             cudaStream_t stream);
+// shifted moments of src (pivot c_s, n_s rows) re-expressed about c_d, added to dst (double-double)
+cudaError_t launch_merge_shifted(double* s, double* s_lo, double* S, double* S_lo, const double* c_d,
+                                 const double* ss, const double* ss_lo, const double* Ss, const double* Ss_lo,
+                                 const double* c_s, const long long* n_s, int p, cudaStream_t stream);
+// float copy of p double pivots (the split kernels' shift), exact for pivots taken from FP32 data
+cudaError_t launch_pivot_to_float(const double* src, float* dst, int p, cudaStream_t stream);
 
 }  // namespace ss

@@ -260,3 +260,68 @@ def test_fragment_pass_tensor_copy_and_column_copies_agree(p):
     assert np.array_equal(r1.S, r2.S) and np.array_equal(r1.s, r2.s)
     cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
     assert rel_fro(a1.cov, cov) < 2e-6
+
+
+# --------------------------------------------------------------------------- merging shifted contexts
+@pytest.mark.parametrize("mode", [G.STATS_FP64_SHIFTED, G.STATS_FP32, G.STATS_BF16X3, G.STATS_BF16X4])
+@pytest.mark.parametrize("p", [16, 64, 96])
+def test_merge_shifted_modes(mode, p):
+    """Two disjoint row ranges in two contexts (different pivots: each its own first row), merged,
+    against one context over all rows and against the oracle; the merged context then takes more rows."""
+    n = 60_011
+    X = independent_table(500 + p, n, p)
+    if mode == G.STATS_FP64_SHIFTED:
+        dt, Xd = G.STATS_F64, X.astype(np.float64)
+    else:
+        dt, Xd = G.STATS_F32, X
+    h1, h2 = 20_000, 45_000
+    def ctx_on(rows):
+        c = G.stats_init(G.Config([dt] * p, mode, [0] * p))
+        if rows.shape[0]:
+            G.stats_accumulate(c, [torch.from_numpy(np.ascontiguousarray(rows[:, j])).cuda() for j in range(p)],
+                               rows.shape[0])
+        return c
+    a, b, c = ctx_on(Xd[:h1]), ctx_on(Xd[h1:h2]), ctx_on(Xd[h2:])
+    G.stats_merge(a, b)
+    G.stats_merge(a, c)
+    raw = G.stats_raw(a)
+    an = G.stats_finalize(a)
+    st = O.stats_columns([Xd[:, j].astype(np.float64) for j in range(p)])
+    cov = O.cov_twopass_columns([Xd[:, j].astype(np.float64) for j in range(p)])
+    assert raw.n == n
+    assert np.max(np.abs(raw.s - st.s_float()) / np.abs(st.s_float())) < (1e-12 if mode == G.STATS_FP64_SHIFTED
+                                                                         else 1e-11)
+    # tolerances of each mode on one context (the tiled kernel's BF16x3 for p > 64 lacks the
+    # diagonal L^T L term: 3e-5)
+    tol = {G.STATS_FP64_SHIFTED: 1e-12, G.STATS_FP32: 1e-4, G.STATS_BF16X4: 2e-6,
+           G.STATS_BF16X3: 2e-6 if p <= 64 else 3e-5}[mode]
+    err = rel_fro(an.cov, cov)
+    print(f"\nmerge mode={mode} p={p}: cov rel-Frobenius error {err:.3e}")
+    assert err < tol
+    for x in (a, b, c):
+        x.close()
+
+
+def test_merge_into_empty_and_export_import_shifted():
+    """An empty context takes the other's pivot on merge; export/import keeps the pivot, and the
+    imported context can take more rows of the same table."""
+    n, p = 40_000, 32
+    X = independent_table(600, n, p)
+    cols = lambda R: [torch.from_numpy(np.ascontiguousarray(R[:, j])).cuda() for j in range(p)]
+    cfg = G.Config([G.STATS_F32] * p, G.STATS_BF16X4, [0] * p)
+    full = G.stats_init(cfg)
+    G.stats_accumulate(full, cols(X), n)
+    part = G.stats_init(cfg)
+    G.stats_accumulate(part, cols(X[:25_000]), 25_000)
+    empty = G.stats_init(cfg)
+    G.stats_merge(empty, part)
+    blob = G.stats_export(empty)
+    imp = G.stats_import(blob, p, G.STATS_BF16X4)
+    G.stats_accumulate(imp, cols(X[25_000:]), n - 25_000)
+    a1 = G.stats_finalize(full)
+    a2 = G.stats_finalize(imp)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    assert rel_fro(a2.cov, cov) < 2e-6 and rel_fro(a1.cov, cov) < 2e-6
+    assert G.stats_raw(imp).n == n
+    for x in (full, part, empty, imp):
+        x.close()
