@@ -231,12 +231,10 @@ int32_t stats_num_analysis_columns(const stats_ctx* ctx);
  * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
 
-/* Tuning knob of STATS_BF16X3 / STATS_BF16X4 (16..4096, a multiple of 16).  For
- * p > 64: rows a warp accumulates in the tensor cores' FP32 accumulators before
- * adding them into its (hi, lo) pairs (default 64; the error grows about linearly
- * with it).  For p <= 64 every 16 rows are a fresh tensor chain whatever the knob;
- * it caps the rows of round-to-nearest FP32 accumulation before the (hi, lo) pairs
- * (default 16384).  Errors: EINVAL. */
+/* Tuning knob of STATS_BF16X3 / STATS_BF16X4 (16..4096, a multiple of 16): rows of
+ * round-to-nearest FP32 accumulation of a warp before its (hi, lo) pairs (default
+ * 1024 for p > 64, 16384 for p <= 64).  Every 16-row block is a fresh tensor-core
+ * chain whatever the knob.  Errors: EINVAL. */
 stats_status stats_set_flush_rows(stats_ctx* ctx, int32_t rows);
 
 /* ---------------------------------------------------------------------------

@@ -512,9 +512,9 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
       c->split_grid = g;
       c->d_split_ticket = reinterpret_cast<unsigned int*>(c->d_split_slots + split_slot_floats(g));
     }
-    // FP32 tensor accumulation error grows with the rows summed before a flush (measured:
-    // about linear); narrow tables flush every 16 rows, wide ones (flush cost ~ p^2) every 64
-    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : (c->p <= 64 ? 16 : 64);
+    // every 16-row K block is a fresh tensor chain; the FP32 accumulators go into (hi, lo)
+    // pairs every 1024 rows of a warp
+    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : 1024;
     S.nrows = nrows;
     S.slots = c->d_split_slots;
     S.ticket = c->d_split_ticket;
@@ -932,7 +932,7 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
       c->split_grid = g;
       c->d_split_ticket = reinterpret_cast<unsigned int*>(c->d_split_slots + split_slot_floats(g));
     }
-    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : (c->p <= 64 ? 16 : 64);
+    S.flush_rows = c->flush_rows > 0 ? c->flush_rows : 1024;
     S.nrows = nrows[t];
     S.slots = c->d_split_slots;
     S.ticket = c->d_split_ticket;

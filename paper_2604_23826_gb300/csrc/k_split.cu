@@ -8,9 +8,12 @@
 // and split r = h + l with h = bf16(r), l = bf16(r - h).  Then
 //   S' = sum_rows r r^T  ~  H^T H + H^T L + L^T H      (BF16x3)
 //                         + L^T L                      (BF16x4)
-// with FP32 accumulation on the tensor cores (mma.sync m16n8k16 bf16).  Every
-// `flush_rows` rows of a warp the FP32 accumulators are added into FP32
-// (hi, lo) pairs with TwoSum, so long sums keep ~48 bits.  Column sums
+// with FP32 accumulation on the tensor cores (mma.sync m16n8k16 bf16): every
+// 16-row K block is a fresh chain, smallest products first, added into FP32
+// accumulators rounding to nearest (the tensor core's own accumulation
+// truncates); every `flush_rows` rows of a warp those are added into FP32
+// (hi, lo) pairs with TwoSum, so long sums keep ~48 bits.  BF16x3 keeps L^T L
+// on the diagonal sub-tiles (the positive bias of the dropped term's diagonal).  Column sums
 // s' = sum r come from the same products with an extra operand column of ones.
 //
 // Work split: the p x p output is cut into T x T tiles (T = 32 or 64) and only
@@ -163,18 +166,24 @@ __device__ __forceinline__ void split_block(const Cols& cols, const SplitParams&
 #pragma unroll
           for (int nj = 0; nj < 4; ++nj) {
             if (diag_sub && 8 * nj + 7 < 16 * mi) continue;  // below the diagonal
-            mma_bf16_16816(acc[mi][nj], ah0, ah1, ah2, ah3, BH.r[nj], BH.q[nj]);
-            mma_bf16_16816(acc[mi][nj], ah0, ah1, ah2, ah3, BL.r[nj], BL.q[nj]);
-            mma_bf16_16816(acc[mi][nj], al0, al1, al2, al3, BH.r[nj], BH.q[nj]);
-            if (X4) mma_bf16_16816(acc[mi][nj], al0, al1, al2, al3, BL.r[nj], BL.q[nj]);
+            // a fresh chain per K block, smallest products first, added to the FP32
+            // accumulators rounding to nearest; BF16x3 keeps L^T L on diagonal sub-tiles
+            // (the positive bias of its diagonal)
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            if (X4 || diag_sub) mma_bf16_16816(d, al0, al1, al2, al3, BL.r[nj], BL.q[nj]);
+            mma_bf16_16816(d, al0, al1, al2, al3, BH.r[nj], BH.q[nj]);
+            mma_bf16_16816(d, ah0, ah1, ah2, ah3, BL.r[nj], BL.q[nj]);
+            mma_bf16_16816(d, ah0, ah1, ah2, ah3, BH.r[nj], BH.q[nj]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[mi][nj][c] += d[c];
           }
           if (diag_sub) {
             // column sums: A rows (columns of X) against a ones column; H^T 1 + L^T 1 = sum (h + l)
-            float t4[4] = {sacc[mi][0], sacc[mi][1], sacc[mi][2], sacc[mi][3]};
-            mma_bf16_16816(t4, ah0, ah1, ah2, ah3, ones_b, ones_b);
+            float t4[4] = {0.f, 0.f, 0.f, 0.f};
             mma_bf16_16816(t4, al0, al1, al2, al3, ones_b, ones_b);
+            mma_bf16_16816(t4, ah0, ah1, ah2, ah3, ones_b, ones_b);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) sacc[mi][c] = t4[c];
+            for (int c = 0; c < 4; ++c) sacc[mi][c] += t4[c];
           }
         }
         if (++since >= flush_kblocks) {
