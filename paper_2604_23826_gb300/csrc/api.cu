@@ -66,6 +66,8 @@ struct stats_ctx {
   unsigned int* d_core_ticket = nullptr;
   int core_grid = 0;
   float* d_fshift = nullptr;            // BF16X3/X4: pivot as float
+  float* d_wide_slots = nullptr;        // BF16X3/X4, p > 64 on tcgen05: per-CTA slots
+  int wide_grid_alloc = 0;
   float* d_split_slots = nullptr;       // BF16X3/X4 scratch: warp slots
   unsigned int* d_split_ticket = nullptr;
   int split_grid = 0;
@@ -76,6 +78,7 @@ struct stats_ctx {
   int tmap_box = 0;
   bool tmap_ok = false;
   alignas(64) CUtensorMap tmap{};
+  void* d_tmap = nullptr;               // device copy of tmap for the wide kernel
   bool shift_set = false;
   double* d_out = nullptr;              // finalize result
   double* d_work = nullptr;             // finalize scratch
@@ -310,7 +313,8 @@ EncodeTiledFn encode_tiled() {
 // A 2D tensor map over p FP32 columns that sit a fixed, 16-byte-multiple stride apart
 // (column j at cols[0] + j * stride), box = rows x P columns; false when the columns
 // are not laid out that way or the map cannot be made.
-bool table_tensor_map(const void* const* cols, int p, int64_t nrows, int P, int rows, CUtensorMap* out) {
+bool table_tensor_map(const void* const* cols, int p, int64_t nrows, int P, int rows, CUtensorMap* out,
+                      bool swizzle128 = false) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn || nrows <= 0 || nrows >= (int64_t(1) << 31) || !aligned16(cols[0])) return false;
   const char* c0 = static_cast<const char*>(cols[0]);
@@ -323,7 +327,8 @@ bool table_tensor_map(const void* const* cols, int p, int64_t nrows, int P, int 
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(rows), static_cast<cuuint32_t>(P)};
   const cuuint32_t estr[2] = {1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<char*>(c0), dim, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -468,6 +473,70 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
   return STATS_OK;
 }
 
+// Wide FP32 tables (p > 64) whose columns sit one 16-byte-multiple stride apart go to the
+// tcgen05 kernel through a 2D tensor map (box 32 rows x 128 columns); others to the
+// tiled split kernel.
+bool wide_eligible(stats_ctx* c, const void* const* dcols, int64_t nrows) {
+  if (c->p <= 64 || c->p > 1280 || nrows <= 0 || nrows >= (int64_t(1) << 31)) return false;
+  const int rows = wide_rows_per_stage(), bcols = wide_block_cols();
+  const int64_t stride = static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0]);
+  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == rows) {
+    bool ok = c->tmap_ok;
+    for (int j = 2; ok && j < c->p; ++j)
+      if (static_cast<const char*>(dcols[j]) - static_cast<const char*>(dcols[0]) != j * stride) ok = false;
+    return ok;
+  }
+  c->tmap_ok = table_tensor_map(dcols, c->p, nrows, bcols, rows, &c->tmap, true);  // 128-byte rows, swizzled
+  c->tmap_base = dcols[0];
+  c->tmap_stride = stride;
+  c->tmap_rows = nrows;
+  c->tmap_box = rows;
+  return c->tmap_ok;
+}
+
+stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
+  if (!c->shift_set) {
+    SplitParams S{};
+    for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
+    S.p = c->p;
+    S.shift = c->d_fshift;
+    CK(c, launch_split_shift(S, c->d_shift, st));
+    c->shift_set = true;
+  }
+  const int grid = wide_grid(c->p, c->sms);
+  if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
+    if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
+    c->d_wide_slots = nullptr;
+    CK(c, cudaMalloc(&c->d_wide_slots,
+                     static_cast<size_t>(grid) * kWideSlotPairs * 2 * sizeof(float) + grid * sizeof(int)));
+    c->wide_grid_alloc = grid;
+  }
+  int* progress = reinterpret_cast<int*>(c->d_wide_slots + static_cast<size_t>(grid) * kWideSlotPairs * 2);
+  CK(c, cudaMemsetAsync(progress, 0, grid * sizeof(int), st));
+  // the tensor map travels in the kernel parameters' ctx-owned device copy
+  if (!c->d_tmap) CK(c, cudaMalloc(&c->d_tmap, sizeof(CUtensorMap)));
+  CK(c, cudaMemcpyAsync(c->d_tmap, &c->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  WideParams W{};
+  W.tmap = c->d_tmap;
+  W.shift = c->d_fshift;
+  W.slots = c->d_wide_slots;
+  W.progress = progress;
+  W.acc_s = c->d_fs;
+  W.acc_s_lo = c->d_fs_lo;
+  W.acc_S = c->d_fS;
+  W.acc_S_lo = c->d_fS_lo;
+  W.acc_n = c->d_fn;
+  W.status = c->d_status;
+  W.nrows = nrows;
+  W.p = c->p;
+  W.nunits = wide_units(c->p, W.unit_i, W.unit_j, kWideMaxUnits);
+  if (W.nunits <= 0) return STATS_EINVAL;
+  const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
+  W.flush_stages = std::max(1, flush_rows / wide_rows_per_stage());
+  CK(c, launch_wide(W, c->mode == STATS_BF16X4, grid, st));
+  return STATS_OK;
+}
+
 stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
   if (nrows == 0) return STATS_OK;
   const int grid = default_grid(c);
@@ -486,6 +555,9 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64) {
     std::vector<Gram32Job> jobs{{c, dcols, nrows}};
     stats_status s = run_gram32(jobs, st);
+    if (s != STATS_OK) return s;
+  } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && wide_eligible(c, dcols, nrows)) {
+    stats_status s = run_wide(c, dcols, nrows, st);
     if (s != STATS_OK) return s;
   } else if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
     SplitParams S{};
@@ -635,6 +707,8 @@ void free_ctx(stats_ctx* c) {
   cudaFree(c->d_fshift);
   cudaFree(c->d_core_slots);
   cudaFree(c->d_split_slots);
+  cudaFree(c->d_wide_slots);
+  cudaFree(c->d_tmap);
   cudaFree(c->d_out);
   cudaFree(c->d_work);
   if (c->h_out) cudaFreeHost(c->h_out);
@@ -879,10 +953,14 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
-      if (c->p <= 64)
+      if (c->p <= 64) {
         g32.push_back({c, dcols[t], nrows[t]});
-      else
+      } else if (wide_eligible(c, dcols[t], nrows[t])) {
+        s = launch_pass(c, dcols[t], nrows[t], st);  // one tcgen05 launch per wide table
+        if (s != STATS_OK) return s;
+      } else {
         split_idx.push_back(t);
+      }
     } else {
       s = stats_accumulate(c, dcols[t], nrows[t], stream);
       if (s != STATS_OK) return s;

@@ -164,6 +164,35 @@ cudaError_t launch_gram32(const Gram32Launch& L, int P, bool x4, int grid, cudaS
 cudaError_t launch_gram32_shift(const Gram32Table* tabs, const int* which, int count, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
+// Wide FP32 tables (p > 64) on tcgen05 (k_wide.cu): 128 x 128 column-block units of
+// the upper block triangle, one unit per CTA, a 2D tensor map over the columns.
+// ---------------------------------------------------------------------------
+constexpr int kWideSlotPairs = 128 * 128 + 2 * 128;  // (hi, lo) pairs of a CTA's slot
+constexpr int kWideMaxUnits = 64;                    // p <= 1280
+struct WideParams {
+  const void* tmap;          // 2D tensor map: dims (nrows, p), box (32 rows, 128 columns)
+  const float* shift;        // p pivots (device)
+  float* slots;              // grid * kWideSlotPairs pairs of scratch
+  double* acc_s;             // ctx accumulators (shifted), double-double
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+  unsigned int* status;      // the ctx's device status word (DEV_* bits)
+  int* progress;             // grid ints, zero at launch: stages each CTA has issued
+  int64_t nrows;
+  int32_t p;
+  int32_t nunits;
+  int32_t flush_stages;      // 32-row stages between FP32 -> (hi, lo) flushes
+  int32_t unit_i[kWideMaxUnits], unit_j[kWideMaxUnits];
+};
+int wide_grid(int p, int sms);  // a multiple of the unit count, at most sms
+int wide_units(int p, int* ui, int* uj, int max_units);
+int wide_rows_per_stage();
+int wide_block_cols();
+cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // CUDA-core comparators for any width: FP64 (raw / shifted) and FP32-core.
 // ---------------------------------------------------------------------------
 constexpr int kCoreSlotDoubles = 2 * (32 * 32 + 32);

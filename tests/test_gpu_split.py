@@ -323,3 +323,47 @@ def test_merge_into_empty_and_export_import_shifted():
     assert G.stats_raw(imp).n == n
     for x in (full, part, empty, imp):
         x.close()
+
+
+# --------------------------------------------------------------------------- wide tables on tcgen05
+def block_cols(X):
+    """Columns of X as rows of one [p, ld] device block (ld a multiple of 4 floats): the layout
+    that the wide tcgen05 pass reads with 2D tensor copies."""
+    n, p = X.shape
+    ld = (n + 3) // 4 * 4
+    blk = torch.zeros((p, ld), dtype=torch.float32, device="cuda")
+    blk[:, :n] = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    return blk, [blk[j, :n] for j in range(p)]
+
+
+@pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
+@pytest.mark.parametrize("p,n", [(96, 40_000), (128, 33), (200, 100_003), (256, 40_000), (160, 20_011)])
+def test_wide_tcgen05_pass(mode, p, n):
+    """p > 64 from a [p, ld] block (the tcgen05 pass): against the oracle, and against the tiled
+    kernel on the same values (separate column allocations)."""
+    X = correlated_table(9 + p, n, p) if p >= 200 else independent_table(900 + p, n, p)
+    blk, cols = block_cols(X)
+    raw, an = run_cols(cols, n, mode)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    st = O.stats_columns([X[:, j].astype(np.float64) for j in range(p)])
+    err = rel_fro(an.cov, cov)
+    print(f"\nwide tcgen05 mode={mode} p={p} n={n}: cov rel-Frobenius error {err:.3e}")
+    assert raw.n == n
+    assert np.max(np.abs(raw.s - st.s_float()) / np.abs(st.s_float())) < 1e-9
+    # BF16x3 drops the off-diagonal of L^T L, sums of products of rounding residuals that
+    # cancel only statistically (~1/sqrt(n)): 2e-6 from n ~ 1000 rows on
+    tol = 2e-6 if (mode == G.STATS_BF16X4 or n >= 1000) else 2e-5
+    assert err < tol
+    sep = [torch.from_numpy(np.ascontiguousarray(X[:, j])).cuda() for j in range(p)]
+    _, an2 = run_cols(sep, n, mode)
+    assert rel_fro(an.cov, an2.cov) < tol
+
+
+def test_wide_tcgen05_reproducible_and_ragged():
+    """Two identical calls give identical bits; a row count ending inside a stage."""
+    n, p = 70_001, 160
+    X = independent_table(950, n, p)
+    blk, cols = block_cols(X)
+    r1, _ = run_cols(cols, n, G.STATS_BF16X3)
+    r2, _ = run_cols(cols, n, G.STATS_BF16X3)
+    assert np.array_equal(r1.S, r2.S) and np.array_equal(r1.s, r2.s)
