@@ -208,6 +208,18 @@ stats_status stats_raw(stats_ctx* ctx, int64_t* n, double* s, double* S_upper, s
 stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals, double* evecs,
                             int32_t pca_on);
 
+/* stats_finalize for many contexts in one launch (one thread block per context; the
+ * FP64 eigen-solver of each block is what a single call costs, so many contexts cost
+ * about one call per SM-load instead of one call each).  Synchronises every context.
+ * For context i the caller-owned HOST outputs mean[i], cov[i], corr[i], evals[i],
+ * evecs[i] are laid out as in stats_finalize; any of the five arrays may be NULL, and
+ * so may any entry.  Outputs of contexts with fewer than two rows are left untouched.
+ * Errors: EINVAL (bad arguments, or some context has n < 2: the others are still
+ * written), the errors of stats_sync for any context. */
+stats_status stats_finalize_batched(stats_ctx* const* ctxs, int32_t count, int32_t pca_on, double* const* mean,
+                                    double* const* cov, double* const* corr, double* const* evals,
+                                    double* const* evecs);
+
 /* Checkpoint: serialise the accumulator and configuration into buf (len bytes).
  * With buf == NULL, *len receives the size needed.  Synchronises.
  * Errors: EINVAL (buffer too small: *len set to the size needed). */

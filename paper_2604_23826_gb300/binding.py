@@ -321,6 +321,24 @@ def stats_finalize(ctx: Ctx, pca_on: int = 0) -> Analysis:
     return Analysis(mean, cov, corr, ev, V)
 
 
+def stats_finalize_batched(ctxs: Sequence[Ctx], pca_on: int = 0) -> list:
+    """stats_finalize for every context in one launch; returns one Analysis per context."""
+    L = load()
+    L.stats_finalize_batched.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 5
+    L.stats_finalize_batched.restype = ctypes.c_int
+    n = len(ctxs)
+    outs = []
+    for c in ctxs:
+        pa = stats_num_analysis_columns(c)
+        outs.append(Analysis(np.zeros(pa), np.zeros((pa, pa)), np.zeros((pa, pa)), np.zeros(pa), np.zeros((pa, pa))))
+    handles = np.fromiter((c.handle.value for c in ctxs), dtype=np.uint64, count=n)
+    ptrs = [np.fromiter((getattr(a, f).ctypes.data for a in outs), dtype=np.uint64, count=n)
+            for f in ("mean", "cov", "corr", "evals", "evecs")]
+    _check(L.stats_finalize_batched(handles.ctypes.data, n, pca_on, *[x.ctypes.data for x in ptrs]),
+           "stats_finalize_batched")
+    return outs
+
+
 def stats_export(ctx: Ctx) -> bytes:
     n = ctypes.c_size_t(0)
     _check(load().stats_export(ctx.handle, None, ctypes.byref(n)), "stats_export(size)")

@@ -665,8 +665,8 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
   return STATS_OK;
 }
 
-stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
-  FinalParams F{};
+void build_final_params(const stats_ctx* c, int want_pca, int pca_on, FinalParams& F) {
+  F = FinalParams{};
   F.p = c->p;
   F.mode = c->mode == STATS_EXACT ? 0 : 1;
   F.pca_on = pca_on;
@@ -691,6 +691,11 @@ stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
                 : nullptr;
   F.out = c->d_out;
   F.work = c->d_work;
+}
+
+stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
+  FinalParams F;
+  build_final_params(c, want_pca, pca_on, F);
   cudaStream_t st = c->last;
   CK(c, launch_finalize(F, st));
   CK(c, cudaMemcpyAsync(c->h_out, c->d_out, c->lay.total * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1201,6 +1206,60 @@ stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* c
   if (evals) memcpy(evals, h + L.evals, sizeof(double) * pa);
   if (evecs) memcpy(evecs, h + L.evecs, sizeof(double) * pa * pa);
   return STATS_OK;
+}
+
+stats_status stats_finalize_batched(stats_ctx* const* ctxs, int32_t count, int32_t pca_on, double* const* mean,
+                                    double* const* cov, double* const* corr, double* const* evals,
+                                    double* const* evecs) {
+  if (count < 0 || (count > 0 && !ctxs) || (pca_on != 0 && pca_on != 1)) return STATS_EINVAL;
+  if (count == 0) return STATS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return STATS_EINVAL;
+    stats_status st = stats_sync(ctxs[i]);
+    if (st != STATS_OK) return st;
+  }
+  const bool want_pca = evals || evecs;
+  std::vector<FinalParams> params(count);
+  std::vector<size_t> off(count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    off[i] = total;
+    total += static_cast<size_t>(ctxs[i]->lay.total);
+  }
+  stats_ctx* c0 = ctxs[0];
+  const size_t pbytes = round256(count * sizeof(FinalParams));
+  void* dbuf = nullptr;
+  CK(c0, cudaMalloc(&dbuf, pbytes + total * sizeof(double)));
+  double* dout = reinterpret_cast<double*>(static_cast<char*>(dbuf) + pbytes);
+  for (int i = 0; i < count; ++i) {
+    build_final_params(ctxs[i], want_pca ? 1 : 0, pca_on, params[i]);
+    params[i].out = dout + off[i];  // the work scratch stays per context
+  }
+  std::vector<double> h(total);
+  cudaError_t e = cudaMemcpy(dbuf, params.data(), count * sizeof(FinalParams), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_finalize_batched(reinterpret_cast<const FinalParams*>(dbuf), count, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), dout, total * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dbuf);
+  if (e != cudaSuccess) return cuda_fail(c0, e);
+  stats_status ret = STATS_OK;
+  for (int i = 0; i < count; ++i) {
+    const stats_ctx* c = ctxs[i];
+    const double* r = h.data() + off[i];
+    const FinalLayout& L = c->lay;
+    const size_t pa = c->pa;
+    int64_t nrows = 0;
+    memcpy(&nrows, r + L.n, sizeof(nrows));  // the row count is stored as an integer
+    if (nrows < 2) {  // no covariance for fewer than two rows
+      ret = STATS_EINVAL;
+      continue;
+    }
+    if (mean && mean[i]) memcpy(mean[i], r + L.mean, sizeof(double) * pa);
+    if (cov && cov[i]) memcpy(cov[i], r + L.cov, sizeof(double) * pa * pa);
+    if (corr && corr[i]) memcpy(corr[i], r + L.corr, sizeof(double) * pa * pa);
+    if (evals && evals[i]) memcpy(evals[i], r + L.evals, sizeof(double) * pa);
+    if (evecs && evecs[i]) memcpy(evecs[i], r + L.evecs, sizeof(double) * pa * pa);
+  }
+  return ret;
 }
 
 // Checkpoint image: magic, version, p, mode, has_bounds, dtypes, ident, lo, hi,

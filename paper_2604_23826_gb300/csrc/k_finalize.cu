@@ -262,7 +262,7 @@ __device__ void jacobi_block(double* A, double* V, int pa, double* evals, double
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 1) finalize_kernel(const __grid_constant__ FinalParams P) {
+__device__ void finalize_body(const FinalParams& P) {
   __shared__ long long G[kDigits * kDigits];
   __shared__ int s_amap[256];  // analysis column index -> table column
   __shared__ int s_pa;
@@ -444,6 +444,21 @@ __global__ void __launch_bounds__(kThreads, 1) finalize_kernel(const __grid_cons
 }
 
 }  // namespace
+
+__global__ void __launch_bounds__(kThreads, 1) finalize_kernel(const __grid_constant__ FinalParams P) {
+  finalize_body(P);
+}
+
+// many contexts at once: block b finalizes Ps[b] (each with its own scratch and output)
+__global__ void __launch_bounds__(kThreads, 1) finalize_batched_kernel(const FinalParams* __restrict__ Ps) {
+  finalize_body(Ps[blockIdx.x]);
+}
+
+cudaError_t launch_finalize_batched(const FinalParams* d_params, int count, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  finalize_batched_kernel<<<count, kThreads, 0, stream>>>(d_params);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream) {
   finalize_kernel<<<1, kThreads, 0, stream>>>(P);

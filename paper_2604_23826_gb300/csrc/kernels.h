@@ -267,6 +267,8 @@ __host__ __device__ inline FinalLayout final_layout(int p, int pa) {
 // flags: [0] an exact integer entry did not fit 128 bits, [1] zero-variance columns,
 //        [2] Jacobi sweeps, [3] eigenpairs computed (1) or not (0)
 cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream);
+// d_params: count FinalParams in device memory, one block each
+cudaError_t launch_finalize_batched(const FinalParams* d_params, int count, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Table 1 generator and misc.

@@ -367,3 +367,33 @@ def test_wide_tcgen05_reproducible_and_ragged():
     r1, _ = run_cols(cols, n, G.STATS_BF16X3)
     r2, _ = run_cols(cols, n, G.STATS_BF16X3)
     assert np.array_equal(r1.S, r2.S) and np.array_equal(r1.s, r2.s)
+
+
+# --------------------------------------------------------------------------- batched finalize
+def test_finalize_batched_matches_single():
+    """Many contexts of different widths and modes finalized in one launch: identical to
+    finalizing each alone; a context with one row is reported and skipped."""
+    rng = np.random.default_rng(5)
+    ctxs, singles = [], []
+    for t, (p, mode) in enumerate([(8, G.STATS_BF16X4), (16, G.STATS_BF16X3), (33, G.STATS_BF16X4),
+                                   (64, G.STATS_BF16X3), (96, G.STATS_BF16X4), (12, G.STATS_FP64_SHIFTED),
+                                   (40, G.STATS_FP32)] * 3):
+        n = int(rng.integers(1_000, 20_000))
+        X = independent_table(2000 + t, n, p)
+        dt = G.STATS_F64 if mode == G.STATS_FP64_SHIFTED else G.STATS_F32
+        Xd = X.astype(np.float64) if dt == G.STATS_F64 else X
+        c = G.stats_init(G.Config([dt] * p, mode, [0] * p))
+        G.stats_accumulate(c, [torch.from_numpy(np.ascontiguousarray(Xd[:, j])).cuda() for j in range(p)], n)
+        ctxs.append(c)
+    for pca_on in (0, 1):
+        singles = [G.stats_finalize(c, pca_on) for c in ctxs]
+        batched = G.stats_finalize_batched(ctxs, pca_on)
+        for a, b in zip(singles, batched):
+            for f in ("mean", "cov", "corr", "evals", "evecs"):
+                assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    one = G.stats_init(G.Config([G.STATS_F32] * 8, G.STATS_BF16X4, [0] * 8))
+    G.stats_accumulate(one, [torch.ones(1, device="cuda") for _ in range(8)], 1)
+    with pytest.raises(G.StatsError):
+        G.stats_finalize_batched(ctxs[:2] + [one])
+    for c in ctxs + [one]:
+        c.close()
