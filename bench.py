@@ -601,7 +601,8 @@ def run_wide(args, rank: int, world: int, local_rank: int):
               "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": m["GB_per_s"], "peak": peak, "unit": "GB/s", "frac": m["hbm_frac"],
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
-            "kernel": MODE_KERNEL[main_mode], "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
+            "kernel": "wide_kernel (tcgen05, TMEM accumulators)" if main_mode.startswith("BF16") else
+            MODE_KERNEL[main_mode], "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
             "tensor_tflops_useful": flops_row * n / (m["ms"] / 1e3) / 1e12, "tensor_peak_tflops": tflops}
     t_ms = torch.tensor([m["ms"]], dtype=torch.float64, device=dev)
     if world > 1:
