@@ -41,7 +41,7 @@ BYTES_PER_ROW = {0: 60, 1: 44}
 # DRAM traffic per row of the exact pass (dram__bytes_read.sum + dram__bytes_write.sum over
 # the rows of one ncu capture, profiles/exact_pass_table1_L32_n1e8.md), with the hash of the
 # kernel sources it was taken on; reported as null once those sources change.
-NCU_TRAFFIC = {"bytes_per_row": 60.038, "src_hash": "30ea4c2294c05516"}
+NCU_TRAFFIC = {"bytes_per_row": 60.038, "src_hash": "30ea4c2294c05516", "layout": "L32"}
 
 
 def kernel_src_hash() -> str:
@@ -376,7 +376,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         peak = 6800.0
     achieved = n * bpr / (kernel_ms / 1e3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["bytes_per_row"] and NCU_TRAFFIC["src_hash"] == kernel_src_hash():
+    if (NCU_TRAFFIC["bytes_per_row"] and NCU_TRAFFIC["src_hash"] == kernel_src_hash()
+            and NCU_TRAFFIC["layout"] == args.layout):
         traffic = NCU_TRAFFIC["bytes_per_row"] * n
     out = {
         "metric": METRIC, "value": world * n / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,

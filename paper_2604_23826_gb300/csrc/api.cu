@@ -137,7 +137,10 @@ bool int_field(int32_t dt, bool bounded, double lo, double hi, ColPlan& cp) {
     cp.is_signed = 1;
   }
   cp.k = std::min(cp.k, dtype_bytes(dt));
-  if (cp.k == dtype_bytes(dt)) cp.is_signed = 1;  // a full-width field is the dtype's own two's complement
+  // An 8-byte field leaves no bits above it to range-check, so it is the dtype's own two's
+  // complement.  A narrower full-width field with a non-negative range stays unsigned: the
+  // sign-extended value of a negative entry then spills past the field and is rejected.
+  if (cp.k == 8) cp.is_signed = 1;
   return true;
 }
 

@@ -159,6 +159,48 @@ def test_exact_range_error_rejects_call():
     assert again.S_exact == good.S_exact
 
 
+def _l16_host_columns(seed, n):
+    """Table 1 rows from the oracle's generator, typed as the L16 layout (int16 / int32 / int64 / f64)."""
+    iv, rv = O.table1_rows(seed, 0, n)
+    out = []
+    for j, dt in enumerate(G.table1_torch_dtypes(G.STATS_T1_L16)):
+        src = rv[:, j] if j in REAL else iv[:, j]
+        out.append(np.ascontiguousarray(src.astype(torch.empty(0, dtype=dt).numpy().dtype)))
+    return out
+
+
+@pytest.mark.parametrize("n", [9, 961, 100_003])
+def test_exact_l16_int16_top_of_range(n):
+    """L16 through the Table 1 converter: ragged sizes, and I (int16, declared [0, 65535]) at 32767,
+    the largest value its dtype holds, against the oracle's exact sums of the same columns."""
+    host = _l16_host_columns(13, n)
+    host[9][n // 2] = 32767
+    host[9][0] = 32000
+    with _ctx(G.STATS_T1_L16) as ctx:
+        G.stats_accumulate(ctx, [torch.from_numpy(c).cuda() for c in host], n)
+        raw = G.stats_raw(ctx)
+    _check_exact(raw, O.stats_columns(host))
+
+
+def test_exact_l16_negative_int16_rejected():
+    """A negative int16 in a column declared non-negative gives STATS_ERANGE (the sign-extended
+    value spills past the two-byte field) and leaves the accumulator unchanged."""
+    n = 4099
+    host = _l16_host_columns(14, n)
+    with _ctx(G.STATS_T1_L16) as ctx:
+        G.stats_accumulate(ctx, [torch.from_numpy(c).cuda() for c in host], n)
+        good = G.stats_raw(ctx)
+        host[9][n - 3] = -1
+        G.stats_accumulate(ctx, [torch.from_numpy(c).cuda() for c in host], n)
+        with pytest.raises(G.StatsError) as e:
+            G.stats_sync(ctx)
+        assert e.value.code == G.STATS_ERANGE
+        G.stats_reset(ctx)
+        G.stats_accumulate(ctx, [torch.from_numpy(c).cuda() for c in _l16_host_columns(14, n)], n)
+        again = G.stats_raw(ctx)
+    assert again.S_exact == good.S_exact
+
+
 # --------------------------------------------------------------------------- generic plan
 def test_exact_generic_columns_signed_and_real():
     """A non-Table-1 configuration (signed int16/32/64, a real column) through the generic converter."""
