@@ -335,6 +335,28 @@ bool table_tensor_map(const void* const* cols, int p, int64_t nrows, int P, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// A 3D tensor map over p FP32 columns a fixed, 16-byte-multiple stride apart, each column's
+// rows seen as (32 rows, nrows / 32 chunks): box (32, chunks, cols) with the 128-byte swizzle.
+// Only whole 32-row chunks are mapped (the rest of a column may end the allocation).
+bool table_tensor_map_chunks(const void* const* cols, int p, int64_t nrows, int cols_box, int chunks_box,
+                             CUtensorMap* out) {
+  EncodeTiledFn fn = encode_tiled();
+  const int64_t nchunks = nrows / 32;
+  if (!fn || nchunks < 1 || nchunks >= (int64_t(1) << 31) || !aligned16(cols[0])) return false;
+  const char* c0 = static_cast<const char*>(cols[0]);
+  int64_t stride = p > 1 ? static_cast<const char*>(cols[1]) - c0 : (nrows * 4 + 15) / 16 * 16;
+  if (stride <= 0 || stride % 16 != 0 || stride >= (int64_t(1) << 40)) return false;
+  for (int j = 2; j < p; ++j)
+    if (static_cast<const char*>(cols[j]) - c0 != j * stride) return false;
+  const cuuint64_t dim[3] = {32u, static_cast<cuuint64_t>(nchunks), static_cast<cuuint64_t>(p)};
+  const cuuint64_t strides[2] = {128u, static_cast<cuuint64_t>(stride)};
+  const cuuint32_t box[3] = {32u, static_cast<cuuint32_t>(chunks_box), static_cast<cuuint32_t>(cols_box)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<char*>(c0), dim, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
   if (jobs.empty()) return STATS_OK;
   stats_ctx* c0 = jobs[0].c;
@@ -480,20 +502,20 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
 // tcgen05 kernel through a 2D tensor map (box 32 rows x 128 columns); others to the
 // tiled split kernel.
 bool wide_eligible(stats_ctx* c, const void* const* dcols, int64_t nrows) {
-  if (c->p <= 64 || c->p > 1280 || nrows <= 0 || nrows >= (int64_t(1) << 31)) return false;
+  if (c->p <= 64 || c->p > 1280 || nrows < wide_chunk_rows() || nrows >= (int64_t(1) << 35)) return false;
   const int rows = wide_rows_per_stage(), bcols = wide_block_cols();
   const int64_t stride = static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0]);
-  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == rows) {
+  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == -rows) {
     bool ok = c->tmap_ok;
     for (int j = 2; ok && j < c->p; ++j)
       if (static_cast<const char*>(dcols[j]) - static_cast<const char*>(dcols[0]) != j * stride) ok = false;
     return ok;
   }
-  c->tmap_ok = table_tensor_map(dcols, c->p, nrows, bcols, rows, &c->tmap, true);  // 128-byte rows, swizzled
+  c->tmap_ok = table_tensor_map_chunks(dcols, c->p, nrows, bcols, rows / wide_chunk_rows(), &c->tmap);
   c->tmap_base = dcols[0];
   c->tmap_stride = stride;
   c->tmap_rows = nrows;
-  c->tmap_box = rows;
+  c->tmap_box = -rows;  // negative: the chunked (3D) map of the wide pass
   return c->tmap_ok;
 }
 
@@ -506,24 +528,23 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
     CK(c, launch_split_shift(S, c->d_shift, st));
     c->shift_set = true;
   }
-  const int grid = wide_grid(c->p, c->sms);
+  WideParams W{};
+  const int grid = wide_plan(c->p, c->sms, W);
+  if (grid <= 0) return STATS_EINVAL;
   if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
     if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
     c->d_wide_slots = nullptr;
-    CK(c, cudaMalloc(&c->d_wide_slots,
-                     static_cast<size_t>(grid) * kWideSlotPairs * 2 * sizeof(float) + grid * sizeof(int)));
+    CK(c, cudaMalloc(&c->d_wide_slots, static_cast<size_t>(grid) * kWideSlotPairs * 2 * sizeof(float)));
     c->wide_grid_alloc = grid;
   }
-  int* progress = reinterpret_cast<int*>(c->d_wide_slots + static_cast<size_t>(grid) * kWideSlotPairs * 2);
-  CK(c, cudaMemsetAsync(progress, 0, grid * sizeof(int), st));
   // the tensor map travels in the kernel parameters' ctx-owned device copy
   if (!c->d_tmap) CK(c, cudaMalloc(&c->d_tmap, sizeof(CUtensorMap)));
   CK(c, cudaMemcpyAsync(c->d_tmap, &c->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
-  WideParams W{};
   W.tmap = c->d_tmap;
+  W.base = static_cast<const float*>(dcols[0]);
+  W.ld = (static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0])) / 4;
   W.shift = c->d_fshift;
   W.slots = c->d_wide_slots;
-  W.progress = progress;
   W.acc_s = c->d_fs;
   W.acc_s_lo = c->d_fs_lo;
   W.acc_S = c->d_fS;
@@ -531,11 +552,10 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
   W.acc_n = c->d_fn;
   W.status = c->d_status;
   W.nrows = nrows;
+  W.nfull = nrows / wide_chunk_rows();
   W.p = c->p;
-  W.nunits = wide_units(c->p, W.unit_i, W.unit_j, kWideMaxUnits);
-  if (W.nunits <= 0) return STATS_EINVAL;
   const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
-  W.flush_stages = std::max(1, flush_rows / wide_rows_per_stage());
+  W.flush_chains = std::max(1, flush_rows / wide_chunk_rows());
   CK(c, launch_wide(W, c->mode == STATS_BF16X4, grid, st));
   return STATS_OK;
 }

@@ -5,21 +5,26 @@
 // Considerations" (r = x - c, c = the table's first row).
 //
 // Work split.  The columns are cut into 128-column blocks; the output's upper block
-// triangle is a list of units (I, J), I <= J, each a 128 x 128 block of S'.  CTA b
-// works on unit b % U over the 32-row stages q, q + G/U, ... (q = b / U); the CTAs
-// with the same q (one per unit) stay within a few stages of each other, so the
-// column blocks that two units share are read from HBM once and from L2 by the other.
+// triangle is a list of units (I, J), I <= J, each a 128 x 128 block of S'.  A diagonal
+// unit converts one column block per stage (plus its column sums), the others two, so
+// the units get CTAs in the proportion 2 : 3 of their measured stage times and sweep the
+// rows at about the same speed.  CTA q of a unit with G_u CTAs takes the 64-row stages
+// q, q + G_u, q + 2 G_u, ...  (Making the units wait for one another, so that the column
+// blocks they share come from L2, cost more in stalls than it saved in HBM reads.)
 //
 // In a CTA (320 threads, one per SM):
-//   warp 0      producer: one 2D tensor copy per column block and stage (32 rows x 128
-//               columns, zero past the table's columns, 128-byte swizzle) into a 3-deep
-//               FP32 ring;
-//   warp 1      MMA issuer: per stage, a fresh accumulation chain in one of two TMEM
-//               buffers: L^T L (BF16x4 only), L^T H, H^T L, H^T H, each as two K = 16
-//               tcgen05.mma.kind::f16 (M = N = 128, bf16 operands from shared memory);
-//   warps 2-5   converters: r = x - c (rows past the table: r = 0), h = bf16(r),
-//               l = bf16(r - h), written in the K-major core-matrix layout the MMA reads;
-//               column sums of r and (BF16x3) sums of l^2 for diagonal units;
+//   warp 0      producer: per stage and column block, one 3D tensor copy (32 rows x 2
+//               chunks x 128 columns: 256 contiguous bytes per column, 128-byte swizzle)
+//               into a ring of 3 (two blocks) or 6 (one block) 32 KB stages; the rows past
+//               the last whole 32-row chunk are read by the converters with plain loads;
+//   warps 2-5   converters: r = x - c (rows past the table: 0), h = bf16(r), l = bf16(r - h),
+//               written IN PLACE over the FP32 stage in the K-major core-matrix layout the
+//               MMA reads (each 8-column group's 2 KB of FP32 becomes its h and l core
+//               matrices); column sums of r and (BF16x3) sums of l^2 for diagonal units;
+//   warp 1      MMA issuer: per 32-row chunk a fresh accumulation chain in one of two TMEM
+//               buffers: L^T L (BF16x4 only), L^T H, H^T L, H^T H, each two K = 16
+//               tcgen05.mma.kind::f16 (M = N = 128); the stage is released when its MMAs
+//               complete;
 //   warps 6-9   epilogue: each thread owns one row of the 128 x 128 block (its TMEM
 //               lane), adds every chain into FP32 registers (round to nearest) and, every
 //               flush, into (hi, lo) pairs in the CTA's slot.
@@ -37,15 +42,17 @@ namespace ss {
 
 namespace {
 
-constexpr int kWBlk = 128;           // columns per block
-constexpr int kWRows = 32;           // rows per stage (two K = 16 steps)
-constexpr int kWFStages = 3;         // FP32 ring depth
-constexpr int kWOStages = 2;         // operand ring depth
+constexpr int kWBlk = 128;                    // columns per block
+constexpr int kWChunk = 32;                   // rows per 128-byte line of the tensor copy, and per MMA chain
+constexpr int kWRows = 64;                    // rows per stage
+constexpr int kWChains = kWRows / kWChunk;    // MMA chains per stage
+constexpr int kWBlkBytes = kWBlk * kWRows * 4;  // 32 KB: one block's stage (FP32, then h and l in place)
+constexpr int kWRingBytes = 6 * kWBlkBytes;     // 192 KB
+constexpr int kWMaxStages = 6;
 constexpr int kWThreads = 320;
-constexpr int kWFBytes = kWBlk * kWRows * 4;        // 16 KB: one block's FP32 stage
-constexpr int kWOBytes = kWBlk * kWRows * 2;        // 8 KB: one block's bf16 operand (h or l)
-constexpr uint32_t kWLbo = 128, kWSbo = 512;        // core-matrix strides (K = 32 per stage)
-constexpr int kWTmemCols = 256;                     // two 128-column accumulators
+constexpr uint32_t kWLbo = 256, kWSbo = 2048;   // core-matrix strides: next 8 rows (K), next 8 columns (M)
+constexpr int kWTmemCols = 256;                 // two 128-column accumulators
+constexpr int kWFold = 16;                      // stages of FP32 partial sums of l^2 per (hi, lo) fold
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   uint64_t d = 0;
@@ -72,11 +79,11 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(smem_dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -87,35 +94,6 @@ __device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, volati
     if (*dead) return false;
   }
   return false;
-}
-
-constexpr int kWLead = 32;  // stages a CTA may run ahead of its peers of the other units
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// bounded wait until the CTAs (q, u') of every other unit u' have issued at least `need`
-// stages; `known` caches the slowest peer's count seen last, so the peers' counters are read
-// once every few stages
-__device__ __forceinline__ bool wait_peers(const int* progress, int q, int U, int unit, int64_t need, int& known,
-                                           volatile unsigned int* dead) {
-  if (need <= known) return true;
-  uint32_t i = 0;
-  for (;;) {
-    int mn = 0x7fffffff;
-    for (int u = 0; u < U; ++u)
-      if (u != unit) mn = min(mn, ld_acquire(progress + q * U + u));
-    known = mn;
-    if (need <= mn) return true;
-    if (*dead || ++i > kSpinLimit) return false;
-    __nanosleep(500);
-  }
 }
 
 __device__ __forceinline__ void record_timeout(volatile unsigned int* dead, unsigned int* status) {
@@ -151,36 +129,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Byte offset, inside a block's stage, of FP32 piece `piece` (rows 4 piece .. 4 piece + 3 of
+// the 32-row chunk) of line L (= 2 column + chunk): 128-byte lines, 16-byte pieces XOR-swizzled
+// with the line index (the tensor copy's 128-byte swizzle; the stage is 1024-byte aligned).
+__device__ __forceinline__ uint32_t fp32_piece(int L, int piece) {
+  return static_cast<uint32_t>(L * 128 + ((piece ^ (L & 7)) << 4));
+}
+
 template <bool X4>
 __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constant__ WideParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  // [FP32 ring: kWFStages x 2 blocks x 16 KB][operands: kWOStages x {Ah, Al, Bh, Bl} x 8 KB]
-  uint8_t* fring = smem;
-  uint8_t* oring = smem + kWFStages * 2 * kWFBytes;
-  __shared__ __align__(8) uint64_t f_full[kWFStages], f_empty[kWFStages], o_full[kWOStages], o_empty[kWOStages],
-      d_full[2], d_empty[2], fin;
+  __shared__ __align__(8) uint64_t f_full[kWMaxStages], c_full[kWMaxStages], f_empty[kWMaxStages], d_full[2],
+      d_empty[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ volatile unsigned int s_dead;
-  __shared__ int s_rows[kWFStages];
+  __shared__ int s_rows[kWMaxStages];
   __shared__ float s_piv[2 * kWBlk];  // pivots of the A block, then the B block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int U = P.nunits, Gu = gridDim.x / U;
-  const int unit = blockIdx.x % U, q0 = blockIdx.x / U;
+  const int U = P.nunits;
+  int unit = 0;
+  while (unit + 1 < U && static_cast<int>(blockIdx.x) >= P.unit_first[unit + 1]) ++unit;
+  const int Gu = P.unit_ctas[unit], first = P.unit_first[unit], q0 = blockIdx.x - first;
   const int I = P.unit_i[unit], J = P.unit_j[unit];
   const bool diag = I == J;
   const int nblk = diag ? 1 : 2;
+  const int S = kWRingBytes / (nblk * kWBlkBytes);  // ring depth: 6 or 3
   const int64_t nst = (P.nrows + kWRows - 1) / kWRows;
   const int64_t my = q0 < nst ? (nst - 1 - q0) / Gu + 1 : 0;  // stages of this CTA
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWFStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&f_full[s], 1);
-      mbar_init(&f_empty[s], 4);
-    }
-    for (int s = 0; s < kWOStages; ++s) {
-      mbar_init(&o_full[s], 4);
-      mbar_init(&o_empty[s], 1);
+      mbar_init(&c_full[s], 4);
+      mbar_init(&f_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&d_full[s], 1);
@@ -210,38 +192,30 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int peer_known = 0;
       int64_t k = 0;
       for (; k < my; ++k) {
         const int64_t st = q0 + k * Gu;
-        if (k >= kWFStages && !wait_live(&f_empty[s], ph ^ 1u, &s_dead)) {
-          record_timeout(&s_dead, P.status);
-          break;
-        }
-        // stay within kWLead stages of the CTAs of the other units that take the same rows
-        // (same q): their shared column blocks then come from L2 (all CTAs are resident:
-        // cooperative launch; the slowest never waits)
-        if (U > 1 && k >= kWLead && !wait_peers(P.progress, q0, U, unit, k - kWLead, peer_known, &s_dead)) {
+        if (k >= S && !wait_live(&f_empty[s], ph ^ 1u, &s_dead)) {
           record_timeout(&s_dead, P.status);
           break;
         }
         s_rows[s] = static_cast<int>(min(static_cast<int64_t>(kWRows), P.nrows - st * kWRows));
-        mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(nblk * kWFBytes));
-        uint8_t* dst = fring + s * 2 * kWFBytes;
-        tma_load_2d(dst, P.tmap, static_cast<int>(st * kWRows), I * kWBlk, &f_full[s]);
-        if (!diag) tma_load_2d(dst + kWFBytes, P.tmap, static_cast<int>(st * kWRows), J * kWBlk, &f_full[s]);
-        if (U > 1) st_release(P.progress + blockIdx.x, static_cast<int>(k + 1));
-        if (++s == kWFStages) {
+        mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(nblk * kWBlkBytes));
+        uint8_t* dst = smem + static_cast<size_t>(s) * nblk * kWBlkBytes;
+        const int y = static_cast<int>(st * kWChains);
+        tma_load_3d(dst, P.tmap, 0, y, I * kWBlk, &f_full[s]);
+        if (!diag) tma_load_3d(dst + kWBlkBytes, P.tmap, 0, y, J * kWBlk, &f_full[s]);
+        if (++s == S) {
           s = 0;
           ph ^= 1u;
         }
       }
       // no copy in flight at exit: the last issued stages land
-      for (int d = 0; d < kWFStages && d < k; ++d) {
+      for (int d = 0; d < S && d < k; ++d) {
         int sk = s - 1 - d;
         uint32_t pk = ph;
         while (sk < 0) {
-          sk += kWFStages;
+          sk += S;
           pk ^= 1u;
         }
         mbar_wait_bounded(&f_full[sk], pk);
@@ -250,36 +224,51 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      int so = 0, bd = 0;
-      uint32_t pho = 0, phd = 0;
-      int64_t k = 0;
-      for (; k < my && !s_dead; ++k) {
-        if (!wait_live(&o_full[so], pho, &s_dead) || (k >= 2 && !wait_live(&d_empty[bd], phd ^ 1u, &s_dead))) {
+      int s = 0, bd = 0;
+      uint32_t ph = 0, phd = 0;
+      int64_t chain = 0;
+      for (int64_t k = 0; k < my && !s_dead; ++k) {
+        if (!wait_live(&c_full[s], ph, &s_dead)) {
           record_timeout(&s_dead, P.status);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ob = smem_u32(oring + so * 4 * kWOBytes);
-        const uint32_t ah = ob, al = ob + kWOBytes;
-        const uint32_t bh = diag ? ah : ob + 2 * kWOBytes, bl = diag ? al : ob + 3 * kWOBytes;
-        const uint32_t dt = tmem + static_cast<uint32_t>(bd * kWBlk);
-        uint32_t acc = 0;
-        // smallest products first; each as two K = 16 steps (256 bytes apart along K)
-        if (X4) {
-          for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(al + ks * 256), umma_desc(bl + ks * 256), acc);
+        const uint32_t ab = smem_u32(smem + static_cast<size_t>(s) * nblk * kWBlkBytes);
+        const uint32_t bb = diag ? ab : ab + kWBlkBytes;
+        bool ok = true;
+        for (int ch = 0; ch < kWChains; ++ch, ++chain) {
+          if (chain >= 2 && !wait_live(&d_empty[bd], phd ^ 1u, &s_dead)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dt = tmem + static_cast<uint32_t>(bd * kWBlk);
+          // chain ch: rows 32 ch .. 32 ch + 31 = K groups 4 ch .. 4 ch + 3; K step ks covers K
+          // groups 4 ch + 2 ks and + 1 (h at +0, l at +128 of each 256-byte K group)
+          const uint32_t ah = ab + ch * 4 * 256, al = ah + 128, bh = bb + ch * 4 * 256, bl = bh + 128;
+          uint32_t acc = 0;
+          // smallest products first
+          if (X4) {
+            for (int ks = 0; ks < 2; ++ks, acc = 1)
+              umma_bf16(dt, umma_desc(al + ks * 512), umma_desc(bl + ks * 512), acc);
+          }
+          for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(al + ks * 512), umma_desc(bh + ks * 512), acc);
+          for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 512), umma_desc(bl + ks * 512), acc);
+          for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 512), umma_desc(bh + ks * 512), acc);
+          umma_commit(&d_full[bd]);
+          if (++bd == 2) {
+            bd = 0;
+            phd ^= 1u;
+          }
         }
-        for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(al + ks * 256), umma_desc(bh + ks * 256), acc);
-        for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 256), umma_desc(bl + ks * 256), acc);
-        for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 256), umma_desc(bh + ks * 256), acc);
-        umma_commit(&o_empty[so]);
-        umma_commit(&d_full[bd]);
-        if (++so == kWOStages) {
-          so = 0;
-          pho ^= 1u;
+        umma_commit(&f_empty[s]);  // the stage is free once its MMAs have read it
+        if (!ok) {
+          record_timeout(&s_dead, P.status);
+          break;
         }
-        if (++bd == 2) {
-          bd = 0;
-          phd ^= 1u;
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
         }
       }
       // every issued MMA completes before the tensor memory is released
@@ -287,83 +276,130 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
       mbar_wait_bounded(&fin, 0);
     }
   } else if (warp < 6) {
-    // ---------------------------------------------------------------- converters
-    // The FP32 stage holds a block's 128 columns as 128-byte lines (32 rows) with the
-    // tensor copy's 128-byte swizzle: 16-byte piece j of column c sits at piece j ^ (c & 7).
-    // Per step a warp takes 8 consecutive columns x 4 pieces (lane: column c0 + lane % 8,
-    // piece 4 half + lane / 8): each quarter warp reads one piece of 8 columns and writes 8
-    // consecutive chunks of one core-matrix row, so reads and operand writes are conflict-free.
+    // ---------------------------------------------------------------- converters (in place)
+    // Warp cw owns the 8-column groups g = 4 cw .. 4 cw + 3 of each block.  Group g's FP32
+    // lines (columns 8g .. 8g + 7, two 32-row chunks each) are the 2 KB at g * 2048; they
+    // become the group's core matrices: K group kk (rows 8 kk .. 8 kk + 7) of h at
+    // g * 2048 + kk * 256 and of l at + 128, row c % 8 of each at 16 (c % 8).  Lane: column
+    // sub = lane % 8 of the group and, in step it (0, 1), the whole K group
+    // kk = 4 j + lane / 8 of chunk j = (sub / 4) ^ it (two 16-byte pieces).  A quarter warp's
+    // 8 lanes read 8 distinct swizzled pieces and write 8 distinct core-matrix rows, so both
+    // are free of bank conflicts and no lane needs another's values.  A block's 16 pieces per
+    // lane are all loaded before any h or l is stored over them.
     const int cw = warp - 2;
-    const bool odd = (lane >> 3) & 1;
-    float sh[4], sl[4], qh[4], ql[4];  // column sums of r and of l^2 (diagonal units), (hi, lo)
+    const int sub = lane & 7, qd = lane >> 3;
+    // column sums of r (diagonal units): 4 values at a time in FP32, then (hi, lo);
+    // sums of l^2 (BF16x3), ~2^-16 of the diagonal they correct: FP32 pairs over kWFold stages
+    float sh[4], sl[4], qh[4], ql[4];
+    float2 pq[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) sh[i] = sl[i] = qh[i] = ql[i] = 0.f;
-    int sf = 0, so = 0;
-    uint32_t phf = 0, pho = 0;
+    for (int i = 0; i < 4; ++i) {
+      sh[i] = sl[i] = qh[i] = ql[i] = 0.f;
+      pq[i] = make_float2(0.f, 0.f);
+    }
+    auto fold_squares = [&]() {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        two_sum(qh[i], ql[i], pq[i].x + pq[i].y);
+        pq[i] = make_float2(0.f, 0.f);
+      }
+    };
+    int since = 0;
+    const int64_t tail = P.nrows - P.nfull * kWChunk;  // rows after the last whole chunk (< 32)
+    int s = 0;
+    uint32_t ph = 0;
     for (int64_t k = 0; k < my; ++k) {
-      bool ok = wait_live(&f_full[sf], phf, &s_dead) && (k < kWOStages || wait_live(&o_empty[so], pho ^ 1u, &s_dead));
-      ok = __all_sync(0xffffffffu, ok);  // the warp decides together (shuffles follow)
+      const bool ok = __all_sync(0xffffffffu, wait_live(&f_full[s], ph, &s_dead));
       if (!ok) {
         if (lane == 0) record_timeout(&s_dead, P.status);
         break;
       }
-      const int rows = s_rows[sf];
-      const uint8_t* fb = fring + sf * 2 * kWFBytes;
-      uint8_t* ob = oring + so * 4 * kWOBytes;
+      const int64_t st = q0 + k * Gu;
+      const int rows = s_rows[s];
+      uint8_t* stage = smem + static_cast<size_t>(s) * nblk * kWBlkBytes;
+      const int64_t jt = P.nfull - st * kWChains;  // chunk of the stage that holds the tail, if 0 or 1
       for (int blk = 0; blk < nblk; ++blk) {
-        const float* src = reinterpret_cast<const float*>(fb + blk * kWFBytes);
-        uint8_t* oh = ob + (2 * blk) * kWOBytes;
-        uint8_t* ol = ob + (2 * blk + 1) * kWOBytes;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int c = 32 * cw + 8 * (i & 3) + (lane & 7);  // column within the block
-          const int piece = 4 * (i >> 2) + (lane >> 3);      // rows 4 piece .. 4 piece + 3
-          const float4 x = *reinterpret_cast<const float4*>(src + c * kWRows + 4 * (piece ^ (c & 7)));
-          const float cp = s_piv[blk * kWBlk + c];
-          float r[4] = {x.x - cp, x.y - cp, x.z - cp, x.w - cp};
-          if (rows < kWRows) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (4 * piece + e >= rows) r[e] = 0.f;
+        uint8_t* base = stage + blk * kWBlkBytes;
+        const int col0 = (blk ? J : I) * kWBlk;
+        if (tail > 0 && (jt == 0 || jt == 1)) {
+          // the tail chunk is past the tensor map (zero-filled): this warp's 32 columns by plain loads
+          const int c = 32 * cw + lane;
+          const int L = 2 * c + static_cast<int>(jt);
+          if (col0 + c < P.p) {
+            const float* src = P.base + static_cast<int64_t>(col0 + c) * P.ld + P.nfull * kWChunk;
+            for (int t = 0; t < static_cast<int>(tail); ++t)
+              *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
           }
-          const uint32_t h01 = pack_bf16x2(r[0], r[1]), h23 = pack_bf16x2(r[2], r[3]);
-          const float e0 = r[0] - bf_lo(h01), e1 = r[1] - bf_hi(h01), e2 = r[2] - bf_lo(h23), e3 = r[3] - bf_hi(h23);
-          const uint32_t l01 = pack_bf16x2(e0, e1), l23 = pack_bf16x2(e2, e3);
-          if (diag && blk == 0) {
-            two_sum(sh[i & 3], sl[i & 3], (r[0] + r[1]) + (r[2] + r[3]));
-            if (!X4) two_sum(qh[i & 3], ql[i & 3], (e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3));
+          __syncwarp();
+        }
+        float4 x[4][2][2];
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi)
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int L = 2 * (8 * (4 * cw + gi) + sub) + ((sub >> 2) ^ it);
+            x[gi][it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+            x[gi][it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
           }
-          // lanes (even piece, odd piece) = (lane, lane ^ 8) hold rows 8g..8g+3 and 8g+4..8g+7 of
-          // column c: the even one writes the h chunk, the odd one the l chunk (K-major core
-          // matrices: 8 rows of a column = 16 bytes)
-          const uint32_t s0 = odd ? h01 : l01, s1 = odd ? h23 : l23;
-          const uint32_t t0 = __shfl_xor_sync(0xffffffffu, s0, 8), t1 = __shfl_xor_sync(0xffffffffu, s1, 8);
-          const int g = piece >> 1;
-          const uint32_t off = (c >> 3) * kWSbo + g * kWLbo + (c & 7) * 16;
-          if (!odd) {
-            *reinterpret_cast<uint4*>(oh + off) = make_uint4(h01, h23, t0, t1);
-          } else {
-            *reinterpret_cast<uint4*>(ol + off) = make_uint4(t0, t1, l01, l23);
+        __syncwarp();  // the warp's FP32 is all in registers before its h and l overwrite it
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi) {
+          const int g = 4 * cw + gi;
+          const float ncp = -s_piv[blk * kWBlk + 8 * g + sub];
+          const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int j = (sub >> 2) ^ it;
+            const int row = kWChunk * j + 8 * qd;  // first of the lane's 8 rows within the stage
+            float2 r[4] = {__fadd2_rn(make_float2(x[gi][it][0].x, x[gi][it][0].y), np),
+                           __fadd2_rn(make_float2(x[gi][it][0].z, x[gi][it][0].w), np),
+                           __fadd2_rn(make_float2(x[gi][it][1].x, x[gi][it][1].y), np),
+                           __fadd2_rn(make_float2(x[gi][it][1].z, x[gi][it][1].w), np)};
+            if (rows < kWRows) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (row + 2 * q >= rows) r[q].x = 0.f;
+                if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+              }
+            }
+            uint32_t h[4], l[4];
+            float2 e[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              h[q] = pack_bf16x2(r[q].x, r[q].y);
+              e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+              l[q] = pack_bf16x2(e[q].x, e[q].y);
+            }
+            if (diag) {
+              const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
+              two_sum(sh[gi], sl[gi], a.x + a.y);
+              two_sum(sh[gi], sl[gi], b.x + b.y);
+              if (!X4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pq[gi] = __ffma2_rn(e[q], e[q], pq[gi]);
+              }
+            }
+            uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
+            *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
           }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&f_empty[sf]);
-        mbar_arrive(&o_full[so]);
+      if (lane == 0) mbar_arrive(&c_full[s]);
+      if (diag && !X4 && ++since == kWFold) {
+        since = 0;
+        fold_squares();
       }
-      if (++sf == kWFStages) {
-        sf = 0;
-        phf ^= 1u;
-      }
-      if (++so == kWOStages) {
-        so = 0;
-        pho ^= 1u;
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
       }
     }
     if (diag) {
-      // the 4 lanes of a column (lane % 8 equal) add their pairs (fixed order), lanes 0-7 write
+      fold_squares();
+      // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -376,7 +412,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
           ql[i] += oql;
         }
         if (lane < 8) {
-          const int c = 32 * cw + 8 * i + lane;
+          const int c = 8 * (4 * cw + i) + lane;
           float2* cs = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
                        kWBlk * kWBlk;
           cs[c] = make_float2(sh[i], sl[i]);
@@ -413,7 +449,8 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
     };
     int bd = 0;
     uint32_t phd = 0;
-    for (int64_t k = 0; k < my; ++k) {
+    const int64_t chains = my * kWChains;
+    for (int64_t k = 0; k < chains; ++k) {
       const bool ok = __all_sync(0xffffffffu, wait_live(&d_full[bd], phd, &s_dead));  // .sync.aligned loads follow
       if (!ok) {
         if (lane == 0) record_timeout(&s_dead, P.status);
@@ -435,7 +472,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
         bd = 0;
         phd ^= 1u;
       }
-      if (++since >= P.flush_stages) {
+      if (++since >= P.flush_chains) {
         since = 0;
         flush();
       }
@@ -453,10 +490,10 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
 // The units' CTA slots, in CTA order, into the context's double-double accumulators.
 // Block (unit, part) takes rows part, part + parts, ... of the unit's 128 x 128 block.
 template <bool X4>
-__global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__ WideParams P, int grid, int parts) {
-  const int U = P.nunits, Gu = grid / U;
+__global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__ WideParams P, int parts) {
   const int unit = blockIdx.x / parts, part = blockIdx.x % parts;
   const int I = P.unit_i[unit], J = P.unit_j[unit];
+  const int first = P.unit_first[unit], G = P.unit_ctas[unit];
   const int p = P.p;
   const float2* slots = reinterpret_cast<const float2*>(P.slots);
   for (int m = part; m < kWBlk; m += parts) {
@@ -466,15 +503,14 @@ __global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__
     const int col = J * kWBlk + n;
     if (col < row || col >= p) continue;
     float h = 0.f, l = 0.f;
-    for (int q = 0; q < Gu; ++q) {
-      const float2 x = __ldcg(slots + static_cast<size_t>(q * U + unit) * kWideSlotPairs + m * kWBlk + n);
+    for (int q = 0; q < G; ++q) {
+      const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + m * kWBlk + n);
       two_sum(h, l, x.x);
       two_sum(h, l, x.y);
     }
     if (!X4 && col == row) {  // BF16x3: + the diagonal of L^T L
-      for (int q = 0; q < Gu; ++q) {
-        const float2 x =
-            __ldcg(slots + static_cast<size_t>(q * U + unit) * kWideSlotPairs + kWBlk * kWBlk + kWBlk + m);
+      for (int q = 0; q < G; ++q) {
+        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + kWBlk * kWBlk + kWBlk + m);
         two_sum(h, l, x.x);
         two_sum(h, l, x.y);
       }
@@ -490,8 +526,8 @@ __global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__
     const int c = threadIdx.x, col = I * kWBlk + c;
     if (col < p) {
       float h = 0.f, l = 0.f;
-      for (int q = 0; q < Gu; ++q) {
-        const float2 x = __ldcg(slots + static_cast<size_t>(q * U + unit) * kWideSlotPairs + kWBlk * kWBlk + c);
+      for (int q = 0; q < G; ++q) {
+        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + kWBlk * kWBlk + c);
         two_sum(h, l, x.x);
         two_sum(h, l, x.y);
       }
@@ -507,43 +543,51 @@ __global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__
 
 template <bool X4>
 cudaError_t launch_w(const WideParams& P, int grid, cudaStream_t st) {
-  const int smem = kWFStages * 2 * kWFBytes + kWOStages * 4 * kWOBytes;
+  const int smem = kWRingBytes;
   cudaError_t e = cudaFuncSetAttribute(wide_kernel<X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  // cooperative: the CTAs of different units wait on one another's progress, so all must be
-  // resident at once
-  WideParams Pc = P;
-  void* args[] = {&Pc};
-  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(wide_kernel<X4>), dim3(grid), dim3(kWThreads), args,
-                                  static_cast<size_t>(smem), st);
-  if (e != cudaSuccess) return e;
+  wide_kernel<X4><<<grid, kWThreads, smem, st>>>(P);
   const int parts = 16;
-  wide_merge_kernel<X4><<<P.nunits * parts, 128, 0, st>>>(P, grid, parts);
+  wide_merge_kernel<X4><<<P.nunits * parts, 128, 0, st>>>(P, parts);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int wide_grid(int p, int sms) {
+int wide_plan(int p, int sms, WideParams& W) {
   const int nb = (p + kWBlk - 1) / kWBlk;
-  const int U = nb * (nb + 1) / 2;
-  return U * std::max(1, sms / U);
-}
-
-int wide_units(int p, int* ui, int* uj, int max_units) {
-  const int nb = (p + kWBlk - 1) / kWBlk;
-  int u = 0;
+  int u = 0, weight = 0;
   for (int I = 0; I < nb; ++I)
     for (int J = I; J < nb; ++J) {
-      if (u >= max_units) return -1;
-      ui[u] = I;
-      uj[u] = J;
+      if (u >= kWideMaxUnits) return 0;
+      W.unit_i[u] = I;
+      W.unit_j[u] = J;
+      weight += I == J ? 2 : 3;
       ++u;
     }
-  return u;
+  W.nunits = u;
+  if (u > sms) return 0;
+  // CTAs in proportion to the weights (diagonal 2, others 3), at least one each, at most sms in all
+  int grid = 0;
+  for (int i = 0; i < u; ++i) {
+    const int w = W.unit_i[i] == W.unit_j[i] ? 2 : 3;
+    W.unit_ctas[i] = std::max(1, (sms * w) / weight);
+    grid += W.unit_ctas[i];
+  }
+  for (int i = 0; grid > sms; i = (i + 1) % u)
+    if (W.unit_ctas[i] > 1) {
+      --W.unit_ctas[i];
+      --grid;
+    }
+  for (int i = 0, f = 0; i < u; ++i) {
+    W.unit_first[i] = f;
+    f += W.unit_ctas[i];
+  }
+  return grid;
 }
 
 int wide_rows_per_stage() { return kWRows; }
+int wide_chunk_rows() { return kWChunk; }
 int wide_block_cols() { return kWBlk; }
 
 cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st) {

@@ -165,12 +165,14 @@ cudaError_t launch_gram32_shift(const Gram32Table* tabs, const int* which, int c
 
 // ---------------------------------------------------------------------------
 // Wide FP32 tables (p > 64) on tcgen05 (k_wide.cu): 128 x 128 column-block units of
-// the upper block triangle, one unit per CTA, a 2D tensor map over the columns.
+// the upper block triangle, one unit per CTA, CTAs per unit in proportion to the unit's
+// work, a 3D tensor map over the columns (32-row lines, 64-row stages).
 // ---------------------------------------------------------------------------
 constexpr int kWideSlotPairs = 128 * 128 + 2 * 128;  // (hi, lo) pairs of a CTA's slot
 constexpr int kWideMaxUnits = 64;                    // p <= 1280
 struct WideParams {
-  const void* tmap;          // 2D tensor map: dims (nrows, p), box (32 rows, 128 columns)
+  const void* tmap;          // 3D tensor map: dims (32, nrows / 32, p), box (32, 2, 128), 128-byte swizzle
+  const float* base;         // column 0; column j at base + j * ld
   const float* shift;        // p pivots (device)
   float* slots;              // grid * kWideSlotPairs pairs of scratch
   double* acc_s;             // ctx accumulators (shifted), double-double
@@ -179,16 +181,20 @@ struct WideParams {
   double* acc_S_lo;
   long long* acc_n;
   unsigned int* status;      // the ctx's device status word (DEV_* bits)
-  int* progress;             // grid ints, zero at launch: stages each CTA has issued
   int64_t nrows;
+  int64_t ld;                // floats between consecutive columns (a multiple of 4)
+  int64_t nfull;             // whole 32-row chunks (nrows / 32); the rest is read with plain loads
   int32_t p;
   int32_t nunits;
-  int32_t flush_stages;      // 32-row stages between FP32 -> (hi, lo) flushes
+  int32_t flush_chains;      // 32-row MMA chains between FP32 -> (hi, lo) flushes
   int32_t unit_i[kWideMaxUnits], unit_j[kWideMaxUnits];
+  int32_t unit_first[kWideMaxUnits], unit_ctas[kWideMaxUnits];  // CTAs [first, first + ctas) of each unit
 };
-int wide_grid(int p, int sms);  // a multiple of the unit count, at most sms
-int wide_units(int p, int* ui, int* uj, int max_units);
+// Units of the upper block triangle and their CTAs (diagonal units weigh 2, the others 3);
+// returns the grid (at most sms), or 0 when p has more units than kWideMaxUnits or sms.
+int wide_plan(int p, int sms, WideParams& W);
 int wide_rows_per_stage();
+int wide_chunk_rows();
 int wide_block_cols();
 cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st);
 

@@ -337,7 +337,8 @@ def block_cols(X):
 
 
 @pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
-@pytest.mark.parametrize("p,n", [(96, 40_000), (128, 33), (200, 100_003), (256, 40_000), (160, 20_011)])
+@pytest.mark.parametrize("p,n", [(96, 40_000), (128, 33), (200, 100_003), (256, 40_000), (160, 20_011),
+                                 (256, 32_007), (130, 64 * 77 + 32)])
 def test_wide_tcgen05_pass(mode, p, n):
     """p > 64 from a [p, ld] block (the tcgen05 pass): against the oracle, and against the tiled
     kernel on the same values (separate column allocations)."""
@@ -357,6 +358,23 @@ def test_wide_tcgen05_pass(mode, p, n):
     sep = [torch.from_numpy(np.ascontiguousarray(X[:, j])).cuda() for j in range(p)]
     _, an2 = run_cols(sep, n, mode)
     assert rel_fro(an.cov, an2.cov) < tol
+
+
+def test_wide_tcgen05_long_paced():
+    """Enough 64-row stages per CTA that the units pace one another: against the oracle, and
+    chunked into three calls of uneven length (ragged tails inside a stage each time)."""
+    n, p = 300_003, 160
+    X = independent_table(960, n, p)
+    blk, cols = block_cols(X)
+    raw, an = run_cols(cols, n, G.STATS_BF16X3)
+    cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+    assert rel_fro(an.cov, cov) < 2e-6
+    ctx = G.stats_init(G.Config([G.STATS_F32] * p, G.STATS_BF16X3, [0] * p))
+    for a, b in ((0, 100_004), (100_004, 100_036), (100_036, n)):  # 16-byte aligned starts
+        G.stats_accumulate(ctx, [blk[j, a:b] for j in range(p)], b - a)
+    an2 = G.stats_finalize(ctx)
+    ctx.close()
+    assert rel_fro(an2.cov, cov) < 2e-6
 
 
 def test_wide_tcgen05_reproducible_and_ragged():
