@@ -12,12 +12,13 @@
 // q, q + G_u, q + 2 G_u, ...  (Making the units wait for one another, so that the column
 // blocks they share come from L2, cost more in stalls than it saved in HBM reads.)
 //
-// In a CTA (320 threads, one per SM):
+// In a CTA (512 threads in four warpgroups, one CTA per SM; after the start the epilogue's
+// warpgroup holds 200 registers per thread and the others 104):
 //   warp 0      producer: per stage and column block, one 3D tensor copy (32 rows x 2
 //               chunks x 128 columns: 256 contiguous bytes per column, 128-byte swizzle)
 //               into a ring of 3 (two blocks) or 6 (one block) 32 KB stages; the rows past
 //               the last whole 32-row chunk are read by the converters with plain loads;
-//   warps 2-5   converters: r = x - c (rows past the table: 0), h = bf16(r), l = bf16(r - h),
+//   warps 4-11  converters: r = x - c (rows past the table: 0), h = bf16(r), l = bf16(r - h),
 //               written IN PLACE over the FP32 stage in the K-major core-matrix layout the
 //               MMA reads (each 8-column group's 2 KB of FP32 becomes its h and l core
 //               matrices); column sums of r and (BF16x3) sums of l^2 for diagonal units;
@@ -25,7 +26,7 @@
 //               buffers: L^T L (BF16x4 only), L^T H, H^T L, H^T H, each two K = 16
 //               tcgen05.mma.kind::f16 (M = N = 128); the stage is released when its MMAs
 //               complete;
-//   warps 6-9   epilogue: each thread owns one row of the 128 x 128 block (its TMEM
+//   warps 12-15 epilogue: each thread owns one row of the 128 x 128 block (its TMEM
 //               lane), adds every chain into FP32 registers (round to nearest) and, every
 //               flush, into (hi, lo) pairs in the CTA's slot.
 // A second kernel adds each unit's CTA slots, in CTA order, into the context's
@@ -49,7 +50,9 @@ constexpr int kWChains = kWRows / kWChunk;    // MMA chains per stage
 constexpr int kWBlkBytes = kWBlk * kWRows * 4;  // 32 KB: one block's stage (FP32, then h and l in place)
 constexpr int kWRingBytes = 6 * kWBlkBytes;     // 192 KB
 constexpr int kWMaxStages = 6;
-constexpr int kWThreads = 320;
+constexpr int kWThreads = 512;                  // four warpgroups
+constexpr int kWConv = 8;                       // converter warps (4 .. 11), two 8-column groups each
+constexpr int kWRegsLow = 104, kWRegsEpi = 200; // per-thread registers after the split: 3 x 104 + 200 = 4 x 128
 constexpr uint32_t kWLbo = 256, kWSbo = 2048;   // core-matrix strides: next 8 rows (K), next 8 columns (M)
 constexpr int kWTmemCols = 256;                 // two 128-column accumulators
 constexpr int kWFold = 16;                      // stages of FP32 partial sums of l^2 per (hi, lo) fold
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&f_full[s], 1);
-      mbar_init(&c_full[s], 4);
+      mbar_init(&c_full[s], kWConv);
       mbar_init(&f_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
@@ -187,6 +190,10 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
+  // Registers: launched at 128 per thread; warpgroup 3 (the epilogue's 128 FP32 accumulators)
+  // takes 200, warpgroups 0-2 give up to 104 (per SMSP: 3 x 24 released, 72 taken).  Each
+  // warpgroup executes its setmaxnreg as a whole, in one branch.
+  if (warp < 12) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWRegsLow));
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
@@ -275,31 +282,32 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
       umma_commit(&fin);
       mbar_wait_bounded(&fin, 0);
     }
-  } else if (warp < 6) {
+  } else if (warp >= 4 && warp < 4 + kWConv) {
     // ---------------------------------------------------------------- converters (in place)
-    // Warp cw owns the 8-column groups g = 4 cw .. 4 cw + 3 of each block.  Group g's FP32
+    // Converter warp cw owns the 8-column groups g = 2 cw, 2 cw + 1 of each block.  Group g's FP32
     // lines (columns 8g .. 8g + 7, two 32-row chunks each) are the 2 KB at g * 2048; they
     // become the group's core matrices: K group kk (rows 8 kk .. 8 kk + 7) of h at
     // g * 2048 + kk * 256 and of l at + 128, row c % 8 of each at 16 (c % 8).  Lane: column
     // sub = lane % 8 of the group and, in step it (0, 1), the whole K group
     // kk = 4 j + lane / 8 of chunk j = (sub / 4) ^ it (two 16-byte pieces).  A quarter warp's
     // 8 lanes read 8 distinct swizzled pieces and write 8 distinct core-matrix rows, so both
-    // are free of bank conflicts and no lane needs another's values.  A block's 16 pieces per
+    // are free of bank conflicts and no lane needs another's values.  A block's 8 pieces per
     // lane are all loaded before any h or l is stored over them.
-    const int cw = warp - 2;
+    const int cw = warp - 4;
     const int sub = lane & 7, qd = lane >> 3;
     // column sums of r (diagonal units): 4 values at a time in FP32, then (hi, lo);
     // sums of l^2 (BF16x3), ~2^-16 of the diagonal they correct: FP32 pairs over kWFold stages
-    float sh[4], sl[4], qh[4], ql[4];
-    float2 pq[4];
+    constexpr int NG = 16 / kWConv;  // groups per converter warp
+    float sh[NG], sl[NG], qh[NG], ql[NG];
+    float2 pq[NG];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NG; ++i) {
       sh[i] = sl[i] = qh[i] = ql[i] = 0.f;
       pq[i] = make_float2(0.f, 0.f);
     }
     auto fold_squares = [&]() {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < NG; ++i) {
         two_sum(qh[i], ql[i], pq[i].x + pq[i].y);
         pq[i] = make_float2(0.f, 0.f);
       }
@@ -322,29 +330,29 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
         uint8_t* base = stage + blk * kWBlkBytes;
         const int col0 = (blk ? J : I) * kWBlk;
         if (tail > 0 && (jt == 0 || jt == 1)) {
-          // the tail chunk is past the tensor map (zero-filled): this warp's 32 columns by plain loads
-          const int c = 32 * cw + lane;
+          // the tail chunk is past the tensor map (zero-filled): this warp's 8 NG columns by plain loads
+          const int c = 8 * NG * cw + lane;
           const int L = 2 * c + static_cast<int>(jt);
-          if (col0 + c < P.p) {
+          if (lane < 8 * NG && col0 + c < P.p) {
             const float* src = P.base + static_cast<int64_t>(col0 + c) * P.ld + P.nfull * kWChunk;
             for (int t = 0; t < static_cast<int>(tail); ++t)
               *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
           }
           __syncwarp();
         }
-        float4 x[4][2][2];
+        float4 x[NG][2][2];
 #pragma unroll
-        for (int gi = 0; gi < 4; ++gi)
+        for (int gi = 0; gi < NG; ++gi)
 #pragma unroll
           for (int it = 0; it < 2; ++it) {
-            const int L = 2 * (8 * (4 * cw + gi) + sub) + ((sub >> 2) ^ it);
+            const int L = 2 * (8 * (NG * cw + gi) + sub) + ((sub >> 2) ^ it);
             x[gi][it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
             x[gi][it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
           }
         __syncwarp();  // the warp's FP32 is all in registers before its h and l overwrite it
 #pragma unroll
-        for (int gi = 0; gi < 4; ++gi) {
-          const int g = 4 * cw + gi;
+        for (int gi = 0; gi < NG; ++gi) {
+          const int g = NG * cw + gi;
           const float ncp = -s_piv[blk * kWBlk + 8 * g + sub];
           const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
 #pragma unroll
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
       fold_squares();
       // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < NG; ++i) {
 #pragma unroll
         for (int d = 8; d < 32; d <<= 1) {
           const float oh_ = __shfl_xor_sync(0xffffffffu, sh[i], d), ol_ = __shfl_xor_sync(0xffffffffu, sl[i], d);
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
           ql[i] += oql;
         }
         if (lane < 8) {
-          const int c = 8 * (4 * cw + i) + lane;
+          const int c = 8 * (NG * cw + i) + lane;
           float2* cs = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
                        kWBlk * kWBlk;
           cs[c] = make_float2(sh[i], sl[i]);
@@ -420,8 +428,9 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
         }
       }
     }
-  } else {
-    // ---------------------------------------------------------------- epilogue
+  } else if (warp >= 12) {
+    // ---------------------------------------------------------------- epilogue (warpgroup 3)
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWRegsEpi));
     const int quarter = warp & 3;         // TMEM lanes 32 quarter .. 32 quarter + 31
     const int m = 32 * quarter + lane;    // this thread's row of the 128 x 128 block
     float acc[kWBlk];
