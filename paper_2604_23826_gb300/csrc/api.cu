@@ -529,7 +529,7 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
     c->shift_set = true;
   }
   WideParams W{};
-  const int grid = wide_plan(c->p, c->sms, W);
+  const int grid = wide_plan(c->p, c->sms, c->mode == STATS_BF16X4, W);
   if (grid <= 0) return STATS_EINVAL;
   if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
     if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));

@@ -7,8 +7,8 @@
 // Work split.  The columns are cut into 128-column blocks; the output's upper block
 // triangle is a list of units (I, J), I <= J, each a 128 x 128 block of S'.  A diagonal
 // unit converts one column block per stage (plus its column sums), the others two, so
-// the units get CTAs in the proportion 2 : 3 of their measured stage times and sweep the
-// rows at about the same speed.  CTA q of a unit with G_u CTAs takes the 64-row stages
+// the units get CTAs in the proportion of their measured stage times and sweep the rows
+// at about the same speed.  CTA q of a unit with G_u CTAs takes the 64-row stages
 // q, q + G_u, q + 2 G_u, ...  (Making the units wait for one another, so that the column
 // blocks they share come from L2, cost more in stalls than it saved in HBM reads.)
 //
@@ -24,8 +24,9 @@
 //               matrices); column sums of r and (BF16x3) sums of l^2 for diagonal units;
 //   warp 1      MMA issuer: per 32-row chunk a fresh accumulation chain in one of two TMEM
 //               buffers: L^T L (BF16x4 only), L^T H, H^T L, H^T H, each two K = 16
-//               tcgen05.mma.kind::f16 (M = N = 128); the stage is released when its MMAs
-//               complete;
+//               tcgen05.mma.kind::f16 (M = N = 128); a BF16x3 diagonal unit, whose l operand
+//               holds 2l, takes only H^T (2L) and H^T H (the merge symmetrizes); the stage is
+//               released when its MMAs complete;
 //   warps 12-15 epilogue: each thread owns one row of the 128 x 128 block (its TMEM
 //               lane), adds every chain into FP32 registers (round to nearest) and, every
 //               flush, into (hi, lo) pairs in the CTA's slot.
@@ -259,7 +260,12 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
             for (int ks = 0; ks < 2; ++ks, acc = 1)
               umma_bf16(dt, umma_desc(al + ks * 512), umma_desc(bl + ks * 512), acc);
           }
-          for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(al + ks * 512), umma_desc(bh + ks * 512), acc);
+          if (X4 || !diag) {
+            for (int ks = 0; ks < 2; ++ks, acc = 1)
+              umma_bf16(dt, umma_desc(al + ks * 512), umma_desc(bh + ks * 512), acc);
+          }
+          // (BF16x3 diagonal units: the l operand holds 2l, so this adds 2 H^T L = H^T L + L^T H
+          // up to a transpose, taken in the merge)
           for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 512), umma_desc(bl + ks * 512), acc);
           for (int ks = 0; ks < 2; ++ks, acc = 1) umma_bf16(dt, umma_desc(ah + ks * 512), umma_desc(bh + ks * 512), acc);
           umma_commit(&d_full[bd]);
@@ -376,7 +382,8 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
             for (int q = 0; q < 4; ++q) {
               h[q] = pack_bf16x2(r[q].x, r[q].y);
               e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
-              l[q] = pack_bf16x2(e[q].x, e[q].y);
+              // BF16x3 diagonal units store 2l (exact): one product 2 H^T L replaces H^T L + L^T H
+              l[q] = (diag && !X4) ? pack_bf16x2(2.f * e[q].x, 2.f * e[q].y) : pack_bf16x2(e[q].x, e[q].y);
             }
             if (diag) {
               const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
@@ -517,6 +524,16 @@ __global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__
       two_sum(h, l, x.x);
       two_sum(h, l, x.y);
     }
+    if (!X4 && I == J) {
+      // BF16x3 diagonal unit: the block holds D = H^T H + 2 H^T L; S = (D + D^T) / 2
+      for (int q = 0; q < G; ++q) {
+        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + n * kWBlk + m);
+        two_sum(h, l, x.x);
+        two_sum(h, l, x.y);
+      }
+      h *= 0.5f;
+      l *= 0.5f;
+    }
     if (!X4 && col == row) {  // BF16x3: + the diagonal of L^T L
       for (int q = 0; q < G; ++q) {
         const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + kWBlk * kWBlk + kWBlk + m);
@@ -563,7 +580,10 @@ cudaError_t launch_w(const WideParams& P, int grid, cudaStream_t st) {
 
 }  // namespace
 
-int wide_plan(int p, int sms, WideParams& W) {
+int wide_plan(int p, int sms, bool x4, WideParams& W) {
+  // measured CTA time per stage, diagonal : off-diagonal units (BF16x3 diagonal units run two
+  // products and convert one block, the others three products and two blocks; BF16x4 four)
+  const int wd = x4 ? 7 : 2, wo = x4 ? 8 : 3;
   const int nb = (p + kWBlk - 1) / kWBlk;
   int u = 0, weight = 0;
   for (int I = 0; I < nb; ++I)
@@ -571,15 +591,15 @@ int wide_plan(int p, int sms, WideParams& W) {
       if (u >= kWideMaxUnits) return 0;
       W.unit_i[u] = I;
       W.unit_j[u] = J;
-      weight += I == J ? 2 : 3;
+      weight += I == J ? wd : wo;
       ++u;
     }
   W.nunits = u;
   if (u > sms) return 0;
-  // CTAs in proportion to the weights (diagonal 2, others 3), at least one each, at most sms in all
+  // CTAs in proportion to the weights, at least one each, at most sms in all
   int grid = 0;
   for (int i = 0; i < u; ++i) {
-    const int w = W.unit_i[i] == W.unit_j[i] ? 2 : 3;
+    const int w = W.unit_i[i] == W.unit_j[i] ? wd : wo;
     W.unit_ctas[i] = std::max(1, (sms * w) / weight);
     grid += W.unit_ctas[i];
   }

@@ -190,9 +190,10 @@ struct WideParams {
   int32_t unit_i[kWideMaxUnits], unit_j[kWideMaxUnits];
   int32_t unit_first[kWideMaxUnits], unit_ctas[kWideMaxUnits];  // CTAs [first, first + ctas) of each unit
 };
-// Units of the upper block triangle and their CTAs (diagonal units weigh 2, the others 3);
-// returns the grid (at most sms), or 0 when p has more units than kWideMaxUnits or sms.
-int wide_plan(int p, int sms, WideParams& W);
+// Units of the upper block triangle and their CTAs (in proportion to each unit's measured
+// time per stage in the mode); returns the grid (at most sms), or 0 when p has more units
+// than kWideMaxUnits or sms.
+int wide_plan(int p, int sms, bool x4, WideParams& W);
 int wide_rows_per_stage();
 int wide_chunk_rows();
 int wide_block_cols();
