@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
-    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10"),
+    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10", "table1_file"),
                     default="table1",
                     help="table1: the headline line; tables4096 / wide256 / f32table: the FP32 workloads")
     ap.add_argument("--p", type=int, default=64, help="f32table: columns")
@@ -134,6 +134,41 @@ def gpu_index(local_rank: int) -> str:
         if local_rank < len(ids):
             return ids[local_rank]
     return str(local_rank)
+
+
+def bind_host_to_gpu(local_rank: int) -> dict:
+    """Restrict this process to the host cores attached to its GPU (sysfs local_cpulist of the
+    GPU's PCI function, intersected with the cores the process may use), so that pinned host
+    buffers allocated afterwards are placed on the GPU's own CPU socket: a host -> device copy
+    from the other socket crosses the CPU-to-CPU link first.  Returns what was done."""
+    info = {"bound": False}
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader",
+                              "-i", gpu_index(local_rank)], capture_output=True, text=True, timeout=20)
+        bus = out.stdout.strip().splitlines()[0].strip().lower()
+        dom, rest = bus.split(":", 1)
+        sysdir = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}"
+        info["pci"] = bus
+        with open(os.path.join(sysdir, "local_cpulist")) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        allowed = os.sched_getaffinity(0)
+        info["_previous"] = allowed
+        both = cpus & allowed
+        info["local_cpus"] = spec
+        if both and both != allowed:
+            os.sched_setaffinity(0, both)
+            info["bound"] = True
+        info["cores"] = len(both or allowed)
+    except Exception as e:  # no nvidia-smi or sysfs entry: leave the affinity alone
+        info["error"] = type(e).__name__
+    return info
 
 
 def measured_peaks() -> dict:
@@ -294,6 +329,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if not args.no_e2e:
         n_e2e = n
         host = None
+        affinity = bind_host_to_gpu(local_rank)
         while host is None and n_e2e >= (1 << 24):
             try:
                 host = [torch.empty(n_e2e, dtype=c.dtype, pin_memory=True) for c in cols]
@@ -343,10 +379,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "d2h_bytes_per_step": result_bytes, "rows": n_e2e, "ms_per_step": e2e_ms, "steps": k_e2e,
                    "h2d_GBps_achieved": n_e2e * bpr / (e2e_ms / 1e3) / 1e9, "h2d_GBps_measured_copy": h2d_gbs,
                    "h2d_frac": (n_e2e * bpr / (e2e_ms / 1e3) / 1e9) / h2d_gbs,
-                   "api": "stats_accumulate_host (pinned host columns, double-buffered chunks) + stats_finalize"}
+                   "api": "stats_accumulate_host (pinned host columns, double-buffered chunks) + stats_finalize",
+                   "host_affinity": {k: v for k, v in affinity.items() if not k.startswith("_")}}
             del host
         else:
             e2e = {"value": None, "unit": UNIT, "note": "pinned host allocation failed"}
+        if affinity.get("_previous"):
+            os.sched_setaffinity(0, affinity["_previous"])  # the CPU baseline gets every core again
 
     # ---- reduce over ranks ----
     t = torch.tensor([elapsed_ms, kernel_ms], dtype=torch.float64, device=dev)
@@ -741,6 +780,79 @@ def run_table1_stream(args, rank: int, world: int, local_rank: int):
         print(json.dumps(out), flush=True)
 
 
+def run_table1_file(args, rank: int, world: int, local_rank: int):
+    """Table 1 from a columnar binary file: written once from the generator (untimed), checked
+    the paper's way (header, size, layout; rows from the beginning, middle and end against the
+    generator), then streamed through pinned chunks into the exact pass (timed, file pages
+    cached by the first read)."""
+    import tempfile
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    seed = 1
+    layout = G.STATS_T1_L32 if args.layout == "L32" else G.STATS_T1_L16
+    bpr = BYTES_PER_ROW[layout]
+    n = int(args.n) if args.n != 1e9 else 100_000_000
+    row0 = rank * n
+    affinity = bind_host_to_gpu(local_rank)
+    tmp = tempfile.mkdtemp(prefix="sscol_")
+    path = os.path.join(tmp, f"table1_{rank}.sscol")
+    try:
+        t0 = time.time()
+        G.stats_file_write_table1(path, seed, n, layout, row0=row0)
+        write_s = time.time() - t0
+        t0 = time.time()
+        G.stats_file_check_table1(path, seed, layout, rows_per_region=1 << 16, row0=row0)
+        check_s = time.time() - t0
+        cfg = G.stats_table1_config(layout, row0 + n, G.STATS_EXACT)
+        ms = []
+        with G.stats_init(cfg) as ctx:
+            for step in range(args.warmup + args.steps):
+                G.stats_reset(ctx)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                G.stats_accumulate_file(ctx, path, chunk_rows=args.chunk_rows, stream=stream)
+                an = G.stats_finalize(ctx, 0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if step >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            raw = G.stats_raw(ctx)
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
+        os.rmdir(tmp)
+    step_ms = sum(ms) / len(ms)
+    lo, hi = row0, row0 + n
+    checks = {"sumA": raw.s_exact[0] == hi * (hi + 1) // 2 - lo * (lo + 1) // 2,
+              "sumA2": raw.S_exact[0][0] == (hi * (hi + 1) * (2 * hi + 1) - lo * (lo + 1) * (2 * lo + 1)) // 6,
+              "n": raw.n == n, "corr_diag_one": bool(np.allclose(np.diag(an.corr), 1.0))}
+    gbs = n * bpr / (step_ms / 1e3) / 1e9
+    config = {"workload": f"table1_file_n{n:.0e}_seed{seed}_{args.layout}".replace("+", ""), "rows_per_gpu": n,
+              "p": 12, "layout": args.layout, "bytes_per_row": bpr, "mode": "STATS_EXACT",
+              "chunk_rows": args.chunk_rows,
+              "step": "stats_accumulate_file (pread into pinned chunks, H2D, exact pass) + finalize",
+              "file": "columnar table file on the box's local disk, pages cached after the write",
+              "parallelism": f"rows sharded, {world} replica(s)"}
+    out = _base_line(args, world, METRIC, world * n / (step_ms / 1e3), step_ms, config,
+                     {"bound": "host file read", "achieved": gbs, "peak": None, "unit": "GB/s", "frac": None,
+                      "traffic": None, "kernel": "exact_pass_kernel<ConvT1>", "algorithmic_bytes": n * bpr},
+                     {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (file pass)"]},
+                     args.steps * ((n + args.chunk_rows - 1) // args.chunk_rows + 1), {"checks": checks, "dtype": "int64",
+                            "file": {"write_s": write_s, "check_s": check_s, "read_GBps": gbs,
+                                     "host_affinity": {k: v for k, v in affinity.items() if not k.startswith("_")}}})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -763,6 +875,8 @@ def main():
             run_f32table(args, rank, world, local_rank)
         elif args.workload == "table1_1e10":
             run_table1_stream(args, rank, world, local_rank)
+        elif args.workload == "table1_file":
+            run_table1_file(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -17,8 +17,8 @@ import numpy as np
 from . import build as _build
 
 # ----------------------------------------------------------------------------- constants (stats.h)
-STATS_OK, STATS_EINVAL, STATS_ENOMEM, STATS_ECUDA, STATS_EOVERFLOW, STATS_ETIMEOUT, STATS_ESTATE, STATS_ERANGE = \
-    range(8)
+(STATS_OK, STATS_EINVAL, STATS_ENOMEM, STATS_ECUDA, STATS_EOVERFLOW, STATS_ETIMEOUT, STATS_ESTATE, STATS_ERANGE,
+ STATS_EIO, STATS_EFORMAT, STATS_EMISMATCH) = range(11)
 STATS_I16, STATS_I32, STATS_I64, STATS_F32, STATS_F64 = range(5)
 STATS_EXACT, STATS_FP64, STATS_FP64_SHIFTED, STATS_BF16X3, STATS_BF16X4, STATS_FP32 = range(6)
 STATS_T1_L32, STATS_T1_L16 = 0, 1
@@ -27,7 +27,12 @@ STATS_MAX_P = 256
 
 _NAMES = {STATS_OK: "STATS_OK", STATS_EINVAL: "STATS_EINVAL", STATS_ENOMEM: "STATS_ENOMEM",
           STATS_ECUDA: "STATS_ECUDA", STATS_EOVERFLOW: "STATS_EOVERFLOW", STATS_ETIMEOUT: "STATS_ETIMEOUT",
-          STATS_ESTATE: "STATS_ESTATE", STATS_ERANGE: "STATS_ERANGE"}
+          STATS_ESTATE: "STATS_ESTATE", STATS_ERANGE: "STATS_ERANGE", STATS_EIO: "STATS_EIO",
+          STATS_EFORMAT: "STATS_EFORMAT", STATS_EMISMATCH: "STATS_EMISMATCH"}
+# stats_file.h
+STATS_FILE_HEADER_BYTES = 4096
+STATS_FILE_ALIGN = 4096
+STATS_FILE_MAX_P = 256
 
 DTYPE_BYTES = {STATS_I16: 2, STATS_I32: 4, STATS_I64: 8, STATS_F32: 4, STATS_F64: 8}
 T1_NAMES = ("A", "B", "C", "D", "E", "F", "G", "H", "cotC", "I", "J", "K")
@@ -89,9 +94,17 @@ def load() -> ctypes.CDLL:
     L.stats_gen_table1.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, i32, ctypes.POINTER(vp), vp]
     L.stats_table1_row_bytes.argtypes = [i32]
     L.stats_table1_row_bytes.restype = i32
+    cp = ctypes.c_char_p
+    L.stats_file_write.argtypes = [cp, i32, ctypes.POINTER(i32), i64, ctypes.POINTER(vp)]
+    L.stats_file_write_table1.argtypes = [cp, ctypes.c_uint64, ctypes.c_uint64, i64, i32, i64]
+    L.stats_file_info.argtypes = [cp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.stats_file_read_rows.argtypes = [cp, i64, i64, ctypes.POINTER(vp)]
+    L.stats_file_check_table1.argtypes = [cp, ctypes.c_uint64, ctypes.c_uint64, i32, i64, ctypes.POINTER(i64)]
+    L.stats_accumulate_file.argtypes = [vp, cp, i64, i64, i64, vp]
     for name in ("stats_init", "stats_accumulate", "stats_accumulate_host", "stats_merge", "stats_sync",
                  "stats_reset", "stats_raw", "stats_finalize", "stats_export", "stats_import", "stats_set_grid",
-                 "stats_table1_config", "stats_gen_table1"):
+                 "stats_table1_config", "stats_gen_table1", "stats_file_write", "stats_file_write_table1",
+                 "stats_file_info", "stats_file_read_rows", "stats_file_check_table1", "stats_accumulate_file"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -434,3 +447,62 @@ def parse_noalloc_result(buf: bytes, p: int) -> Raw:
     code = STATS_ERANGE if status & 1 else STATS_ETIMEOUT if status & 2 else \
         STATS_EOVERFLOW if d[flags] != 0.0 else STATS_OK
     return Raw(n, s, S, s_ex, SE, code)
+
+
+# ----------------------------------------------------------------------------- table files (stats_file.h)
+def _path(path) -> bytes:
+    return os.fsencode(path)
+
+
+def stats_file_write(path, dtypes: Sequence[int], nrows: int, hcols: Sequence):
+    """Write an n x p table from host columns (numpy arrays / pinned tensors / addresses)."""
+    p = len(dtypes)
+    dt = (ctypes.c_int32 * p)(*dtypes)
+    _check(load().stats_file_write(_path(path), p, dt, nrows, _ptr_array(hcols)), "stats_file_write")
+
+
+def stats_file_write_table1(path, seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0,
+                            chunk_rows: int = 0):
+    """Write Table 1 rows [row0, row0 + nrows), generated on the current device, to a table file."""
+    _check(load().stats_file_write_table1(_path(path), seed, row0, nrows, layout, chunk_rows),
+           "stats_file_write_table1")
+
+
+def stats_file_info(path):
+    """(p, nrows, dtypes) of a validated table file."""
+    p = ctypes.c_int32(0)
+    n = ctypes.c_int64(0)
+    dt = (ctypes.c_int32 * STATS_FILE_MAX_P)()
+    _check(load().stats_file_info(_path(path), ctypes.byref(p), ctypes.byref(n), dt), "stats_file_info")
+    return p.value, n.value, [dt[j] for j in range(p.value)]
+
+
+_NP_DTYPES = {STATS_I16: np.int16, STATS_I32: np.int32, STATS_I64: np.int64, STATS_F32: np.float32,
+              STATS_F64: np.float64}
+
+
+def stats_file_read_rows(path, row0: int, nrows: int):
+    """Rows [row0, row0 + nrows) of every column, as numpy arrays."""
+    _, _, dts = stats_file_info(path)
+    cols = [np.empty(nrows, dtype=_NP_DTYPES[d]) for d in dts]
+    _check(load().stats_file_read_rows(_path(path), row0, nrows, _ptr_array(cols)), "stats_file_read_rows")
+    return cols
+
+
+def stats_file_check_table1(path, seed: int, layout: int = STATS_T1_L32, rows_per_region: int = 4096,
+                            row0: int = 0) -> int:
+    """The conversion check of a Table 1 file; returns -1, raises StatsError(STATS_EMISMATCH) with
+    .bad_row set to the first differing file row."""
+    bad = ctypes.c_int64(-1)
+    code = load().stats_file_check_table1(_path(path), seed, row0, layout, rows_per_region, ctypes.byref(bad))
+    if code != STATS_OK:
+        err = StatsError(code, "stats_file_check_table1")
+        err.bad_row = bad.value
+        raise err
+    return bad.value
+
+
+def stats_accumulate_file(ctx: Ctx, path, row0: int = 0, nrows: int = -1, chunk_rows: int = 0, stream=None):
+    """Add file rows [row0, row0 + nrows) (nrows < 0: to the end) to ctx through pinned chunks."""
+    _check(load().stats_accumulate_file(ctx.handle, _path(path), row0, nrows, chunk_rows, _stream_handle(stream)),
+           "stats_accumulate_file")

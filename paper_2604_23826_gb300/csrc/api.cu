@@ -11,9 +11,13 @@
 #include <new>
 #include <vector>
 
+#include <unistd.h>
+
 #include "../../include/stats.h"
+#include "../../include/stats_file.h"
 #include <cuda.h>
 
+#include "file_format.h"
 #include "kernels.h"
 
 using namespace ss;
@@ -91,6 +95,9 @@ struct stats_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_done[2] = {nullptr, nullptr};
+  // file streaming: pinned host chunks (free again once ev_copied[b] has completed)
+  void* h_stage[2] = {nullptr, nullptr};
+  size_t h_stage_bytes = 0;
   cudaStream_t last = nullptr;
   int grid = 0;
   int sms = 0;
@@ -742,6 +749,7 @@ void free_ctx(stats_ctx* c) {
   if (c->h_out) cudaFreeHost(c->h_out);
   for (int b = 0; b < 2; ++b) {
     cudaFree(c->d_stage[b]);
+    if (c->h_stage[b]) cudaFreeHost(c->h_stage[b]);
     if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
     if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
   }
@@ -867,6 +875,65 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
 
 }  // namespace
 
+namespace {
+
+// The two device staging buffers of the host- and file-streamed passes (each column of
+// a chunk at stage_off[j], 256-byte aligned) and the copy stream with its events.
+stats_status ensure_staging(stats_ctx* ctx, int64_t chunk_rows) {
+  if (ctx->stage_rows < chunk_rows) {
+    for (int b = 0; b < 2; ++b) {
+      if (ctx->d_stage[b]) CK(ctx, cudaFree(ctx->d_stage[b]));
+      ctx->d_stage[b] = nullptr;
+    }
+    ctx->stage_off.assign(ctx->p, 0);
+    size_t off = 0;
+    for (int j = 0; j < ctx->p; ++j) {
+      ctx->stage_off[j] = off;
+      off += ((static_cast<size_t>(chunk_rows) * dtype_bytes(ctx->dtypes[j]) + 255) / 256) * 256;
+    }
+    for (int b = 0; b < 2; ++b) {
+      cudaError_t e = cudaMalloc(&ctx->d_stage[b], off);
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        ctx->stage_rows = 0;
+        return STATS_ENOMEM;
+      }
+      CK(ctx, e);
+    }
+    ctx->stage_rows = chunk_rows;
+  }
+  if (!ctx->copy_stream) {
+    CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
+    }
+  }
+  return STATS_OK;
+}
+
+// Copy one chunk (hc: p host column pointers at the chunk's first row) into staging
+// buffer b on the copy stream and enqueue its pass on st.
+stats_status enqueue_chunk(stats_ctx* ctx, int b, const void* const* hc, int64_t rows, cudaStream_t st) {
+  std::vector<const void*> dcols(ctx->p);
+  // the pass that last read buffer b must be done before it is overwritten
+  CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
+  for (int j = 0; j < ctx->p; ++j) {
+    const size_t eb = dtype_bytes(ctx->dtypes[j]);
+    char* dst = static_cast<char*>(ctx->d_stage[b]) + ctx->stage_off[j];
+    CK(ctx, cudaMemcpyAsync(dst, hc[j], static_cast<size_t>(rows) * eb, cudaMemcpyHostToDevice, ctx->copy_stream));
+    dcols[j] = dst;
+  }
+  CK(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+  CK(ctx, cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+  const stats_status s = launch_pass(ctx, dcols.data(), rows, st);
+  if (s != STATS_OK) return s;
+  CK(ctx, cudaEventRecord(ctx->ev_done[b], st));
+  return STATS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 stats_status stats_init(stats_ctx** out, const stats_config* cfg) { return create(out, cfg); }
@@ -893,54 +960,80 @@ stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int
   if (chunk_rows == 0) chunk_rows = kDefaultChunkRows;
   chunk_rows = (chunk_rows + 7) & ~int64_t(7);
   if (chunk_rows > nrows) chunk_rows = (nrows + 7) & ~int64_t(7);
-  // (re)allocate the two staging buffers
-  if (ctx->stage_rows < chunk_rows) {
+  s = ensure_staging(ctx, chunk_rows);
+  if (s != STATS_OK) return s;
+  std::vector<const void*> hc(ctx->p);
+  int64_t chunk = 0;
+  for (int64_t r0 = 0; r0 < nrows; r0 += chunk_rows, ++chunk) {
+    const int64_t rows = std::min(chunk_rows, nrows - r0);
+    for (int j = 0; j < ctx->p; ++j)
+      hc[j] = static_cast<const char*>(hcols[j]) + static_cast<size_t>(r0) * dtype_bytes(ctx->dtypes[j]);
+    s = enqueue_chunk(ctx, static_cast<int>(chunk & 1), hc.data(), rows, st);
+    if (s != STATS_OK) return s;
+  }
+  return STATS_OK;
+}
+
+stats_status stats_accumulate_file(stats_ctx* ctx, const char* path, int64_t row0, int64_t nrows,
+                                   int64_t chunk_rows, void* stream) {
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  if (!path || row0 < 0 || chunk_rows < 0) return STATS_EINVAL;
+  FileInfo info;
+  int fd = -1;
+  s = file_open_checked(path, info, &fd);
+  if (s != STATS_OK) return s;
+  struct Closer {
+    int fd;
+    ~Closer() { close(fd); }
+  } closer{fd};
+  if (info.p != ctx->p) return STATS_EINVAL;
+  for (int j = 0; j < ctx->p; ++j)
+    if (info.dtypes[j] != ctx->dtypes[j]) return STATS_EINVAL;
+  if (row0 > info.nrows) return STATS_EINVAL;
+  if (nrows < 0) nrows = info.nrows - row0;
+  if (nrows > info.nrows - row0) return STATS_EINVAL;
+  if (nrows == 0) return STATS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (chunk_rows == 0) chunk_rows = int64_t(1) << 22;
+  chunk_rows = (chunk_rows + 7) & ~int64_t(7);
+  if (chunk_rows > nrows) chunk_rows = (nrows + 7) & ~int64_t(7);
+  s = ensure_staging(ctx, chunk_rows);
+  if (s != STATS_OK) return s;
+  // pinned host chunks laid out like the device staging buffers
+  size_t bytes = 0;
+  for (int j = 0; j < ctx->p; ++j)
+    bytes = std::max(bytes, ctx->stage_off[j] + ((static_cast<size_t>(chunk_rows) * dtype_bytes(ctx->dtypes[j]) + 255) / 256) * 256);
+  if (ctx->h_stage_bytes < bytes) {
     for (int b = 0; b < 2; ++b) {
-      if (ctx->d_stage[b]) CK(ctx, cudaFree(ctx->d_stage[b]));
-      ctx->d_stage[b] = nullptr;
+      CK(ctx, cudaEventSynchronize(ctx->ev_copied[b]));  // no copy still reads the old chunk
+      if (ctx->h_stage[b]) CK(ctx, cudaFreeHost(ctx->h_stage[b]));
+      ctx->h_stage[b] = nullptr;
     }
-    ctx->stage_off.assign(ctx->p, 0);
-    size_t off = 0;
-    for (int j = 0; j < ctx->p; ++j) {
-      ctx->stage_off[j] = off;
-      off += ((static_cast<size_t>(chunk_rows) * dtype_bytes(ctx->dtypes[j]) + 255) / 256) * 256;
-    }
+    ctx->h_stage_bytes = 0;
     for (int b = 0; b < 2; ++b) {
-      cudaError_t e = cudaMalloc(&ctx->d_stage[b], off);
+      const cudaError_t e = cudaHostAlloc(&ctx->h_stage[b], bytes, cudaHostAllocDefault);
       if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return STATS_ENOMEM;
       }
       CK(ctx, e);
     }
-    ctx->stage_rows = chunk_rows;
+    ctx->h_stage_bytes = bytes;
   }
-  if (!ctx->copy_stream) {
-    CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-    for (int b = 0; b < 2; ++b) {
-      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
-      CK(ctx, cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
-    }
-  }
-  std::vector<const void*> dcols(ctx->p);
+  std::vector<void*> hc(ctx->p);
   int64_t chunk = 0;
-  for (int64_t r0 = 0; r0 < nrows; r0 += chunk_rows, ++chunk) {
+  for (int64_t r = 0; r < nrows; r += chunk_rows, ++chunk) {
     const int b = static_cast<int>(chunk & 1);
-    const int64_t rows = std::min(chunk_rows, nrows - r0);
-    // the pass that last read buffer b must be done before it is overwritten
-    CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
-    for (int j = 0; j < ctx->p; ++j) {
-      const size_t eb = dtype_bytes(ctx->dtypes[j]);
-      char* dst = static_cast<char*>(ctx->d_stage[b]) + ctx->stage_off[j];
-      const char* src = static_cast<const char*>(hcols[j]) + static_cast<size_t>(r0) * eb;
-      CK(ctx, cudaMemcpyAsync(dst, src, static_cast<size_t>(rows) * eb, cudaMemcpyHostToDevice, ctx->copy_stream));
-      dcols[j] = dst;
-    }
-    CK(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
-    CK(ctx, cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
-    s = launch_pass(ctx, dcols.data(), rows, st);
+    const int64_t rows = std::min(chunk_rows, nrows - r);
+    // host chunk b is refilled once the copies that last read it have run; meanwhile the
+    // device copies and reduces the other chunk
+    CK(ctx, cudaEventSynchronize(ctx->ev_copied[b]));
+    for (int j = 0; j < ctx->p; ++j) hc[j] = static_cast<char*>(ctx->h_stage[b]) + ctx->stage_off[j];
+    s = file_read_rows(fd, info, row0 + r, rows, hc.data());
     if (s != STATS_OK) return s;
-    CK(ctx, cudaEventRecord(ctx->ev_done[b], st));
+    s = enqueue_chunk(ctx, b, hc.data(), rows, st);
+    if (s != STATS_OK) return s;
   }
   return STATS_OK;
 }
@@ -1399,6 +1492,9 @@ const char* stats_strerror(stats_status st) {
     case STATS_ETIMEOUT: return "a bounded device-side wait expired";
     case STATS_ESTATE: return "context failed earlier or call out of order";
     case STATS_ERANGE: return "a value lay outside the digit field of its declared range";
+    case STATS_EIO: return "a file could not be opened, read or written";
+    case STATS_EFORMAT: return "not a valid table file (header, layout or size)";
+    case STATS_EMISMATCH: return "a sampled file row differs from its source";
     default: return "unknown status";
   }
 }
