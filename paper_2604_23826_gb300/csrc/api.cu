@@ -26,6 +26,9 @@ namespace {
 
 constexpr uint64_t kMagic = 0x3130535441545353ull;  // "SSTATS01"
 constexpr int64_t kDefaultChunkRows = int64_t(1) << 24;
+// In a batch, a 33..64-column table of at least this many rows gets its own tcgen05 launch;
+// smaller ones share the register-fragment launch (one launch costs a few microseconds).
+constexpr int64_t kNarrowBatchMinRows = int64_t(1) << 19;
 
 struct ColPlan {
   int k = 0;         // digit bytes
@@ -80,6 +83,7 @@ struct stats_ctx {
   const void* tmap_base = nullptr;
   int64_t tmap_stride = 0, tmap_rows = 0;
   int tmap_box = 0;
+  int tmap_cols = 0;  // columns per box of the cached map
   bool tmap_ok = false;
   alignas(64) CUtensorMap tmap{};
   void* d_tmap = nullptr;               // device copy of tmap for the wide kernel
@@ -512,7 +516,8 @@ bool wide_eligible(stats_ctx* c, const void* const* dcols, int64_t nrows) {
   if (c->p <= 64 || c->p > 1280 || nrows < wide_chunk_rows() || nrows >= (int64_t(1) << 35)) return false;
   const int rows = wide_rows_per_stage(), bcols = wide_block_cols();
   const int64_t stride = static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0]);
-  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == -rows) {
+  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == -rows &&
+      c->tmap_cols == bcols) {
     bool ok = c->tmap_ok;
     for (int j = 2; ok && j < c->p; ++j)
       if (static_cast<const char*>(dcols[j]) - static_cast<const char*>(dcols[0]) != j * stride) ok = false;
@@ -522,7 +527,29 @@ bool wide_eligible(stats_ctx* c, const void* const* dcols, int64_t nrows) {
   c->tmap_base = dcols[0];
   c->tmap_stride = stride;
   c->tmap_rows = nrows;
-  c->tmap_box = -rows;  // negative: the chunked (3D) map of the wide pass
+  c->tmap_box = -rows;  // negative: a chunked (3D) map
+  c->tmap_cols = bcols;
+  return c->tmap_ok;
+}
+
+// 33 to 64 columns, uniformly strided (one [p, ld] block): the tcgen05 pass of k_narrow.cu.
+bool narrow_eligible(stats_ctx* c, const void* const* dcols, int64_t nrows) {
+  if (c->p <= 32 || c->p > narrow_cols() || nrows < wide_chunk_rows() || nrows >= (int64_t(1) << 35)) return false;
+  const int rows = narrow_rows_per_stage(), bcols = narrow_cols();
+  const int64_t stride = static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0]);
+  if (c->tmap_base == dcols[0] && c->tmap_stride == stride && c->tmap_rows == nrows && c->tmap_box == -rows &&
+      c->tmap_cols == bcols) {
+    bool ok = c->tmap_ok;
+    for (int j = 2; ok && j < c->p; ++j)
+      if (static_cast<const char*>(dcols[j]) - static_cast<const char*>(dcols[0]) != j * stride) ok = false;
+    return ok;
+  }
+  c->tmap_ok = table_tensor_map_chunks(dcols, c->p, nrows, bcols, rows / wide_chunk_rows(), &c->tmap);
+  c->tmap_base = dcols[0];
+  c->tmap_stride = stride;
+  c->tmap_rows = nrows;
+  c->tmap_box = -rows;
+  c->tmap_cols = bcols;
   return c->tmap_ok;
 }
 
@@ -567,6 +594,49 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
   return STATS_OK;
 }
 
+stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
+  if (!c->shift_set) {
+    SplitParams S{};
+    for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
+    S.p = c->p;
+    S.shift = c->d_fshift;
+    CK(c, launch_split_shift(S, c->d_shift, st));
+    c->shift_set = true;
+  }
+  WideParams W{};
+  const int grid = std::max(1, c->sms);
+  W.nunits = 1;
+  W.unit_i[0] = W.unit_j[0] = 0;
+  W.unit_first[0] = 0;
+  W.unit_ctas[0] = grid;
+  if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
+    if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
+    c->d_wide_slots = nullptr;
+    CK(c, cudaMalloc(&c->d_wide_slots, static_cast<size_t>(grid) * kWideSlotPairs * 2 * sizeof(float)));
+    c->wide_grid_alloc = grid;
+  }
+  if (!c->d_tmap) CK(c, cudaMalloc(&c->d_tmap, sizeof(CUtensorMap)));
+  CK(c, cudaMemcpyAsync(c->d_tmap, &c->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  W.tmap = c->d_tmap;
+  W.base = static_cast<const float*>(dcols[0]);
+  W.ld = (static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0])) / 4;
+  W.shift = c->d_fshift;
+  W.slots = c->d_wide_slots;
+  W.acc_s = c->d_fs;
+  W.acc_s_lo = c->d_fs_lo;
+  W.acc_S = c->d_fS;
+  W.acc_S_lo = c->d_fS_lo;
+  W.acc_n = c->d_fn;
+  W.status = c->d_status;
+  W.nrows = nrows;
+  W.nfull = nrows / wide_chunk_rows();
+  W.p = c->p;
+  const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
+  W.flush_chains = std::max(1, flush_rows / narrow_rows_per_stage());  // one chain per stage
+  CK(c, launch_narrow(W, c->mode == STATS_BF16X4, grid, st));
+  return STATS_OK;
+}
+
 stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
   if (nrows == 0) return STATS_OK;
   const int grid = default_grid(c);
@@ -582,6 +652,10 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
     int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
     CK(c, launch_exact(P, c->conv, g, st));
+  } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64 &&
+             narrow_eligible(c, dcols, nrows)) {
+    stats_status s = run_narrow(c, dcols, nrows, st);
+    if (s != STATS_OK) return s;
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64) {
     std::vector<Gram32Job> jobs{{c, dcols, nrows}};
     stats_status s = run_gram32(jobs, st);
@@ -1074,7 +1148,10 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
-      if (c->p <= 64) {
+      if (c->p > 32 && c->p <= 64 && nrows[t] >= kNarrowBatchMinRows && narrow_eligible(c, dcols[t], nrows[t])) {
+        s = run_narrow(c, dcols[t], nrows[t], st);  // large 33..64-column tables: one tcgen05 launch each
+        if (s != STATS_OK) return s;
+      } else if (c->p <= 64) {
         g32.push_back({c, dcols[t], nrows[t]});
       } else if (wide_eligible(c, dcols[t], nrows[t])) {
         s = launch_pass(c, dcols[t], nrows[t], st);  // one tcgen05 launch per wide table

@@ -1,0 +1,431 @@
+// k_narrow.cu -- sufficient statistics of FP32 tables of 33 to 64 columns on the tcgen05
+// tensor cores: arxiv 2604.23826, "Data Representation and Sufficient Statistics" (column
+// sums and X^T X in one streaming pass, partials over row ranges combined), with the shift
+// of "Numerical Considerations" (r = x - c, c = the table's first row).
+//
+// The h and l halves of the split r = h + l (bf16 each) are stacked into one operand of
+// M = 128 rows, 8-column group by 8-column group: operand row 16 g + i is h of column
+// 8 g + i, row 16 g + 8 + i its l (i < 8).  One tcgen05.mma.kind::f16 per 16-row K step then
+// gives every product at once (h(c), l(c): the operand rows of column c):
+//   BF16x4: A = B = the stacked operand (N = 128), and
+//           S[c][d] = D[h(c)][h(d)] + D[h(c)][l(d)] + D[l(c)][h(d)] + D[l(c)][l(d)];
+//   BF16x3: A = the stacked operand, B = its h rows only (N = 64, read at twice the row-group
+//           stride), and S[c][d] = D[h(c)][d] + D[l(c)][d] + D[l(d)][c] (+ sum l^2 on the
+//           diagonal).
+// TMEM lane m accumulates its own row, so each epilogue thread keeps 64 FP32 sums (BF16x4
+// adds the h and l column of each d first); the merge kernel forms S from the per-CTA slots.
+//
+// In a CTA (512 threads, four warpgroups; one CTA per SM):
+//   warp 0      producer: one 3D tensor copy per 64-row stage (32 rows x 2 chunks x 64
+//               columns, 128-byte swizzle, zero past p) into a ring of twelve 16 KB stages;
+//               rows past the last whole 32-row chunk are read by the converters;
+//   warps 4-11  converters, one 8-column group each: the group's 2 KB of FP32 becomes, in
+//               place, its h core matrices (first KB) and l core matrices (second KB), K group
+//               kk at + kk * 128, so a warp writes only what it read; column sums of r and
+//               (BF16x3) sum l^2;
+//   warp 1      MMA issuer: per 64-row stage a fresh chain of four K = 16 MMAs into one of
+//               two TMEM buffers and one commit (each tcgen05 instruction costs the issuing
+//               thread ~65 cycles, so a stage carries as few as possible);
+//   warps 12-15 epilogue: each thread owns TMEM lane m, adds every chain into 64 FP32
+//               registers (round to nearest) and, every flush, into (hi, lo) pairs in the
+//               CTA's slot; on seeing a chain's commit it hands the stage back to the producer.
+// Every wait is bounded: on expiry the CTA records STATS_ETIMEOUT and winds down.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc05.cuh"
+
+namespace ss {
+
+namespace {
+
+using namespace tc05;
+
+constexpr int kNCols = 64;                        // columns of the block
+constexpr int kNChunk = 32;                       // rows per tensor-copy line
+constexpr int kNRows = 64;                        // rows per stage, and per MMA chain (4 K steps)
+constexpr int kNChunks = kNRows / kNChunk;
+constexpr int kNStageBytes = kNCols * kNRows * 4;  // 16 KB: FP32, then h (8 KB) and l (8 KB) in place
+constexpr int kNStages = 12;                      // 192 KB ring
+constexpr int kNThreads = 512;
+constexpr int kNConv = 8;                         // converter warps 4 .. 11
+constexpr int kNRegsLow = 104, kNRegsEpi = 200;   // 3 x 104 + 200 = 4 x 128 per SMSP
+constexpr uint32_t kNLbo = 128, kNSbo = 1024;     // next K group, next 8 operand rows (h, l alternate)
+constexpr int kNTmemCols = 256;
+constexpr int kNFold = 16;                        // stages of FP32 partial sums of l^2 per fold
+constexpr int kNSlotStride = 128;                 // pairs per slot row (the wide pass's slot layout)
+
+template <bool X4>
+__global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_constant__ WideParams P) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t f_full[kNStages], c_full[kNStages], f_empty[kNStages], d_full[2], d_empty[2],
+      fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile unsigned int s_dead;
+  __shared__ int s_rows[kNStages];
+  __shared__ float s_piv[kNCols];
+
+  constexpr int NB = X4 ? 128 : 64;  // accumulator columns of a chain
+  constexpr uint32_t kIdesc = idesc_bf16(128, NB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, q0 = blockIdx.x;
+  const int64_t nst = (P.nrows + kNRows - 1) / kNRows;
+  const int64_t my = q0 < nst ? (nst - 1 - q0) / G + 1 : 0;  // stages of this CTA
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNStages; ++s) {
+      mbar_init(&f_full[s], 1);
+      mbar_init(&c_full[s], kNConv);
+      mbar_init(&f_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&d_full[s], 1);
+      mbar_init(&d_empty[s], 4);
+    }
+    mbar_init(&fin, 1);
+    s_dead = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < kNCols; i += kNThreads) s_piv[i] = i < P.p ? P.shift[i] : 0.f;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kNTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  // registers: warpgroup 3 (the epilogue) takes 200 per thread, warpgroups 0-2 give up to 104
+  if (warp < 12) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kNRegsLow));
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t k = 0;
+      for (; k < my; ++k) {
+        const int64_t st = q0 + k * G;
+        if (k >= kNStages && !wait_live(&f_empty[s], ph ^ 1u, &s_dead)) {
+          record_timeout(&s_dead, P.status);
+          break;
+        }
+        s_rows[s] = static_cast<int>(min(static_cast<int64_t>(kNRows), P.nrows - st * kNRows));
+        mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(kNStageBytes));
+        tma_load_3d(smem + static_cast<size_t>(s) * kNStageBytes, P.tmap, 0, static_cast<int>(st * kNChunks), 0,
+                    &f_full[s]);
+        if (++s == kNStages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      for (int d = 0; d < kNStages && d < k; ++d) {  // no copy in flight at exit
+        int sk = s - 1 - d;
+        uint32_t pk = ph;
+        while (sk < 0) {
+          sk += kNStages;
+          pk ^= 1u;
+        }
+        mbar_wait_bounded(&f_full[sk], pk);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    // The whole warp runs the loop (warp-uniform addresses and descriptors); one elected lane
+    // issues the tcgen05 instructions.
+    int s = 0, bd = 0;
+    uint32_t ph = 0, phd = 0;
+    for (int64_t k = 0; k < my; ++k) {
+      // stage k: converted, and its TMEM buffer drained by the epilogue (stage k - 2)
+      const bool ok = __shfl_sync(0xffffffffu,
+                                  lane == 0 ? (wait_live(&c_full[s], ph, &s_dead) &&
+                                               (k < 2 || wait_live(&d_empty[bd], phd ^ 1u, &s_dead)))
+                                            : false,
+                                  0);
+      if (!ok) {
+        if (lane == 0) record_timeout(&s_dead, P.status);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + static_cast<size_t>(s) * kNStageBytes);
+      const uint32_t dt = tmem + static_cast<uint32_t>(bd * 128);
+      // one fresh chain per stage: K step ks = K groups 2 ks and 2 ks + 1; A = the stacked
+      // operand, B = the same (BF16x4) or its h rows.  The epilogue frees the stage once this
+      // commit has arrived.
+      if (elect_one()) {
+#pragma unroll
+        for (int ks = 0; ks < kNRows / 16; ++ks) {
+          const uint64_t a = desc<kNLbo, kNSbo>(base + ks * 2 * kNLbo);
+          const uint64_t b = X4 ? a : desc<kNLbo, 2 * kNSbo>(base + ks * 2 * kNLbo);
+          mma_bf16(dt, a, b, kIdesc, ks);
+        }
+        umma_commit(&d_full[bd]);
+      }
+      __syncwarp();
+      if (++bd == 2) {
+        bd = 0;
+        phd ^= 1u;
+      }
+      if (++s == kNStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    if (elect_one()) umma_commit(&fin);  // every issued MMA completes before the tensor memory is released
+    __syncwarp();
+    if (lane == 0) mbar_wait_bounded(&fin, 0);
+    __syncwarp();
+  } else if (warp >= 4 && warp < 4 + kNConv) {
+    // ---------------------------------------------------------------- converters
+    // Warp cw owns columns 8 cw .. 8 cw + 7: their FP32 lines L = 2 c + chunk are the 2 KB at
+    // cw * 2048, where its h and l core matrices go.  Lane: column sub = lane % 8 of the group
+    // and, in step it (0, 1), K group kk = 4 j + lane / 8 of chunk j = (sub / 4) ^ it: a quarter
+    // warp reads 8 distinct swizzled 16-byte pieces and writes 8 distinct core-matrix rows (no
+    // bank conflicts).
+    const int cw = warp - 4;
+    const int sub = lane & 7, qd = lane >> 3;
+    const int c = 8 * cw + sub;
+    float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;  // column sums of r and l^2, (hi, lo)
+    float2 pq = make_float2(0.f, 0.f);
+    int since = 0;
+    const int64_t tail = P.nrows - P.nfull * kNChunk;
+    const float ncp = -s_piv[c];
+    const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+    int s = 0;
+    uint32_t ph = 0;
+    for (int64_t k = 0; k < my; ++k) {
+      const bool ok = __all_sync(0xffffffffu, wait_live(&f_full[s], ph, &s_dead));
+      if (!ok) {
+        if (lane == 0) record_timeout(&s_dead, P.status);
+        break;
+      }
+      const int64_t st = q0 + k * G;
+      const int rows = s_rows[s];
+      uint8_t* base = smem + static_cast<size_t>(s) * kNStageBytes;
+      const int64_t jt = P.nfull - st * kNChunks;  // chunk of the stage holding the tail, if 0 or 1
+      if (tail > 0 && (jt == 0 || jt == 1)) {
+        if (lane < 8 && 8 * cw + lane < P.p) {
+          const int cc = 8 * cw + lane;
+          const int L = 2 * cc + static_cast<int>(jt);
+          const float* src = P.base + static_cast<int64_t>(cc) * P.ld + P.nfull * kNChunk;
+          for (int t = 0; t < static_cast<int>(tail); ++t)
+            *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
+        }
+        __syncwarp();
+      }
+      float4 x[2][2];
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int L = 2 * c + ((sub >> 2) ^ it);
+        x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+        x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+      }
+      __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int j = (sub >> 2) ^ it;
+        const int row = kNChunk * j + 8 * qd;
+        float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
+                       __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
+                       __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
+                       __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
+        if (rows < kNRows) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (row + 2 * q >= rows) r[q].x = 0.f;
+            if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+          }
+        }
+        uint32_t h[4], l[4];
+        float2 e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          h[q] = pack_bf16x2(r[q].x, r[q].y);
+          e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+          l[q] = pack_bf16x2(e[q].x, e[q].y);
+        }
+        const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
+        two_sum(sh, sl, a.x + a.y);
+        two_sum(sh, sl, b.x + b.y);
+        if (!X4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
+        }
+        const int kk = 4 * j + qd;
+        uint8_t* hp = base + 2 * cw * kNSbo + kk * kNLbo + sub * 16;
+        *reinterpret_cast<uint4*>(hp) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(hp + kNSbo) = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c_full[s]);
+      if (!X4 && ++since == kNFold) {
+        since = 0;
+        two_sum(qh, ql, pq.x + pq.y);
+        pq = make_float2(0.f, 0.f);
+      }
+      if (++s == kNStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    two_sum(qh, ql, pq.x + pq.y);
+    // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
+#pragma unroll
+    for (int d = 8; d < 32; d <<= 1) {
+      const float oh_ = __shfl_xor_sync(0xffffffffu, sh, d), ol_ = __shfl_xor_sync(0xffffffffu, sl, d);
+      const float oq_ = __shfl_xor_sync(0xffffffffu, qh, d), oql = __shfl_xor_sync(0xffffffffu, ql, d);
+      two_sum(sh, sl, oh_);
+      sl += ol_;
+      two_sum(qh, ql, oq_);
+      ql += oql;
+    }
+    if (lane < 8) {
+      float2* cs = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
+                   128 * kNSlotStride;
+      cs[c] = make_float2(sh, sl);
+      cs[128 + c] = make_float2(qh, ql);
+    }
+  } else if (warp >= 12) {
+    // ---------------------------------------------------------------- epilogue (warpgroup 3)
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kNRegsEpi));
+    const int quarter = warp & 3;
+    const int m = 32 * quarter + lane;  // TMEM lane = operand row: h (m % 16 < 8) or l of column 8 (m / 16) + m % 8
+    float acc[kNCols];
+#pragma unroll
+    for (int i = 0; i < kNCols; ++i) acc[i] = 0.f;
+    float2* slot = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
+                   static_cast<size_t>(m) * kNSlotStride;
+    bool fresh = true;
+    int since = 0;
+    auto flush = [&]() {
+#pragma unroll
+      for (int i0 = 0; i0 < kNCols; i0 += 8) {
+        float2 hl[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(slot + i0 + k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          two_sum(hl[k].x, hl[k].y, acc[i0 + k]);
+          acc[i0 + k] = 0.f;
+          __stcg(slot + i0 + k, hl[k]);
+        }
+        asm volatile("" ::: "memory");
+      }
+      fresh = false;
+    };
+    int bd = 0, se = 0;
+    uint32_t phd = 0;
+    for (int64_t k = 0; k < my; ++k) {
+      const bool ok = __all_sync(0xffffffffu, wait_live(&d_full[bd], phd, &s_dead));  // .sync.aligned loads follow
+      if (!ok) {
+        if (lane == 0) record_timeout(&s_dead, P.status);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the stage's MMAs have completed: its shared memory goes back to the producer
+      if (warp == 12 && lane == 0) mbar_arrive(&f_empty[se]);
+      if (++se == kNStages) se = 0;
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * 128);
+#pragma unroll
+      for (int c0 = 0; c0 < NB; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr + c0, v);
+        if (X4) {  // columns 16 g .. 16 g + 7: h of columns 8 g + i; the next 8: their l
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[c0 / 2 + i] += v[i] + v[8 + i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d_empty[bd]);
+      if (++bd == 2) {
+        bd = 0;
+        phd ^= 1u;
+      }
+      if (++since >= P.flush_chains) {  // flush_chains counts stages here
+        since = 0;
+        flush();
+      }
+    }
+    flush();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kNTmemCols) : "memory");
+  }
+}
+
+// The CTA slots, in CTA order, into the context's double-double accumulators.
+template <bool X4>
+__global__ void __launch_bounds__(64) narrow_merge_kernel(const __grid_constant__ WideParams P, int grid, int parts) {
+  const int p = P.p;
+  const float2* slots = reinterpret_cast<const float2*>(P.slots);
+  const int n = threadIdx.x;
+  auto add = [&](float& h, float& l, int idx) {
+    for (int q = 0; q < grid; ++q) {
+      const float2 x = __ldcg(slots + static_cast<size_t>(q) * kWideSlotPairs + idx);
+      two_sum(h, l, x.x);
+      two_sum(h, l, x.y);
+    }
+  };
+  for (int m = blockIdx.x; m < p; m += parts) {
+    if (n < m || n >= p) continue;
+    const int hm = 16 * (m / 8) + m % 8, hn = 16 * (n / 8) + n % 8;  // operand rows of h(m), h(n)
+    float h = 0.f, l = 0.f;
+    add(h, l, hm * kNSlotStride + n);          // H^T H (BF16x4: + H^T L)
+    add(h, l, (hm + 8) * kNSlotStride + n);    // L^T H (BF16x4: + L^T L)
+    if (!X4) {
+      add(h, l, (hn + 8) * kNSlotStride + m);  // H^T L, from the transposed entry
+      if (n == m) add(h, l, 128 * kNSlotStride + 128 + m);  // + the diagonal of L^T L
+    }
+    const int64_t e = static_cast<int64_t>(m) * p - static_cast<int64_t>(m) * (m - 1) / 2 + (n - m);
+    const double v = static_cast<double>(h) + static_cast<double>(l);
+    const double s = P.acc_S[e] + v;
+    const double bp = s - P.acc_S[e];
+    P.acc_S_lo[e] += (P.acc_S[e] - (s - bp)) + (v - bp);
+    P.acc_S[e] = s;
+  }
+  if (blockIdx.x == 0 && n < p) {  // column sums
+    float h = 0.f, l = 0.f;
+    add(h, l, 128 * kNSlotStride + n);
+    const double v = static_cast<double>(h) + static_cast<double>(l);
+    const double s = P.acc_s[n] + v;
+    const double bp = s - P.acc_s[n];
+    P.acc_s_lo[n] += (P.acc_s[n] - (s - bp)) + (v - bp);
+    P.acc_s[n] = s;
+  }
+  if (blockIdx.x == 0 && n == 0) *P.acc_n += P.nrows;
+}
+
+template <bool X4>
+cudaError_t launch_n(const WideParams& P, int grid, cudaStream_t st) {
+  const int smem = kNStages * kNStageBytes;
+  cudaError_t e = cudaFuncSetAttribute(narrow_kernel<X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  narrow_kernel<X4><<<grid, kNThreads, smem, st>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int parts = 32;
+  narrow_merge_kernel<X4><<<parts, 64, 0, st>>>(P, grid, parts);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int narrow_cols() { return kNCols; }
+int narrow_rows_per_stage() { return kNRows; }
+
+cudaError_t launch_narrow(const WideParams& P, bool x4, int grid, cudaStream_t st) {
+  return x4 ? launch_n<true>(P, grid, st) : launch_n<false>(P, grid, st);
+}
+
+}  // namespace ss

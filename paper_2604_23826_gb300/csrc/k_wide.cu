@@ -39,6 +39,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc05.cuh"
 
 namespace ss {
 
@@ -58,87 +59,25 @@ constexpr uint32_t kWLbo = 256, kWSbo = 2048;   // core-matrix strides: next 8 r
 constexpr int kWTmemCols = 256;                 // two 128-column accumulators
 constexpr int kWFold = 16;                      // stages of FP32 partial sums of l^2 per (hi, lo) fold
 
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>((kWLbo >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>((kWSbo >> 4) & 0x3FFFu) << 32;
-  d |= static_cast<uint64_t>(1) << 46;  // descriptor version; base offset 0, no swizzle
-  return d;
-}
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) { return tc05::desc<kWLbo, kWSbo>(saddr); }
 
 // instruction descriptor: D f32, A and B bf16, both K-major, M = N = 128
-constexpr uint32_t kWIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kWIdesc = tc05::idesc_bf16(128, 128);
 
 __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(kWIdesc), "r"(accumulate)
-      : "memory");
+  tc05::mma_bf16(dtmem, a, b, kWIdesc, accumulate);
 }
 
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(smem_dst)),
-      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, volatile unsigned int* dead) {
-  if (mbar_try_wait(bar, parity)) return true;
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
-    if (*dead) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void record_timeout(volatile unsigned int* dead, unsigned int* status) {
-  *dead = 1;
-  atomicOr(status, DEV_ETIMEOUT);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  uint32_t d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
-
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bp = s - hi;
-  lo += (hi - (s - bp)) + (v - bp);
-  hi = s;
-}
-
-// 16 consecutive TMEM columns of this warp's 32 lanes into registers
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Byte offset, inside a block's stage, of FP32 piece `piece` (rows 4 piece .. 4 piece + 3 of
-// the 32-row chunk) of line L (= 2 column + chunk): 128-byte lines, 16-byte pieces XOR-swizzled
-// with the line index (the tensor copy's 128-byte swizzle; the stage is 1024-byte aligned).
-__device__ __forceinline__ uint32_t fp32_piece(int L, int piece) {
-  return static_cast<uint32_t>(L * 128 + ((piece ^ (L & 7)) << 4));
-}
+using tc05::umma_commit;
+using tc05::tma_load_3d;
+using tc05::wait_live;
+using tc05::record_timeout;
+using tc05::pack_bf16x2;
+using tc05::bf_lo;
+using tc05::bf_hi;
+using tc05::two_sum;
+using tc05::tmem_ld16;
+using tc05::fp32_piece;
 
 template <bool X4>
 __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constant__ WideParams P) {

@@ -198,6 +198,11 @@ int wide_rows_per_stage();
 int wide_chunk_rows();
 int wide_block_cols();
 cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st);
+// 33..64 columns (k_narrow.cu): one 64-column block, h and l stacked into an M = 128 operand;
+// WideParams with a single unit (0, 0) of `grid` CTAs, tmap boxed (32, 2, 64).
+int narrow_cols();
+int narrow_rows_per_stage();
+cudaError_t launch_narrow(const WideParams& P, bool x4, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // CUDA-core comparators for any width: FP64 (raw / shifted) and FP32-core.

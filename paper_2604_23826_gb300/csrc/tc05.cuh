@@ -1,0 +1,109 @@
+// tc05.cuh -- device helpers of the tcgen05 passes (k_wide.cu, k_narrow.cu): UMMA shared-memory
+// descriptors and instruction descriptors, tcgen05.mma / commit / ld, 3D tensor copies,
+// bounded mbarrier waits, bf16 packing and the FP32 two-sum.
+#pragma once
+
+#include "common.cuh"
+
+namespace ss {
+namespace tc05 {
+
+// Shared-memory matrix descriptor of a K-major, unswizzled operand: LBO = byte stride between
+// core matrices adjacent in K, SBO = between core matrices adjacent in M (or N).
+template <uint32_t LBO, uint32_t SBO>
+__device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((LBO >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((SBO >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version; base offset 0, no swizzle
+  return d;
+}
+
+// instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// One lane of the (converged) warp: true for it, false for the others.  Issuing tcgen05
+// instructions from warp-uniform code under this predicate keeps their operands (descriptors,
+// TMEM addresses) in uniform registers.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t r;
+  asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}" : "=r"(r));
+  return r != 0;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(smem_dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, volatile unsigned int* dead) {
+  if (mbar_try_wait(bar, parity)) return true;
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
+    if (*dead) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void record_timeout(volatile unsigned int* dead, unsigned int* status) {
+  *dead = 1;
+  atomicOr(status, DEV_ETIMEOUT);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes into registers
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset, inside a block's stage, of FP32 piece `piece` (rows 4 piece .. 4 piece + 3 of
+// the 32-row chunk) of line L (= 2 column + chunk): 128-byte lines, 16-byte pieces XOR-swizzled
+// with the line index (the tensor copy's 128-byte swizzle; the stage is 1024-byte aligned).
+__device__ __forceinline__ uint32_t fp32_piece(int L, int piece) {
+  return static_cast<uint32_t>(L * 128 + ((piece ^ (L & 7)) << 4));
+}
+
+}  // namespace tc05
+}  // namespace ss

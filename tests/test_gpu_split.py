@@ -360,6 +360,56 @@ def test_wide_tcgen05_pass(mode, p, n):
     assert rel_fro(an.cov, an2.cov) < tol
 
 
+@pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
+@pytest.mark.parametrize("p,n", [(64, 40_000), (33, 33), (48, 100_003), (64, 32_007), (40, 64 * 77 + 32),
+                                 (64, 1_000_001)])
+def test_narrow_tcgen05_pass(mode, p, n):
+    """33..64 columns from a [p, ld] block (the tcgen05 pass with h and l stacked into one M = 128
+    operand): against the oracle, and against the register-fragment pass on the same values
+    (separate column allocations)."""
+    X = independent_table(700 + p, n, p)
+    blk, cols = block_cols(X)
+    raw, an = run_cols(cols, n, mode)
+    st = O.stats_columns([X[:, j].astype(np.float64) for j in range(p)])
+    assert raw.n == n
+    assert np.max(np.abs(raw.s - st.s_float()) / np.abs(st.s_float())) < 1e-9
+    if n >= 2:
+        cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+        err = rel_fro(an.cov, cov)
+        print(f"\nnarrow tcgen05 mode={mode} p={p} n={n}: cov rel-Frobenius error {err:.3e}")
+        tol = 2e-6 if (mode == G.STATS_BF16X4 or n >= 1000) else 2e-5
+        assert err < tol
+        sep = [torch.from_numpy(np.ascontiguousarray(X[:, j])).cuda() for j in range(p)]
+        _, an2 = run_cols(sep, n, mode)
+        assert rel_fro(an.cov, an2.cov) < tol
+
+
+def test_narrow_in_a_batch_and_across_calls():
+    """A batch mixing a large 64-column block (its own tcgen05 launch) with small tables (the shared
+    register-fragment launch); the large table also split into two calls of different paths."""
+    rng = np.random.default_rng(8)
+    big = independent_table(801, 600_001, 64)
+    small = [independent_table(810 + t, int(rng.integers(1000, 50_000)), int(rng.choice([8, 40, 64])))
+             for t in range(6)]
+    tabs = [big] + small
+    blocks = [block_cols(X) for X in tabs]
+    ctxs = [G.stats_init(G.Config([G.STATS_F32] * X.shape[1], G.STATS_BF16X3, [0] * X.shape[1])) for X in tabs]
+    G.stats_accumulate_batched(ctxs, [b[1] for b in blocks], [X.shape[0] for X in tabs])
+    for X, c in zip(tabs, ctxs):
+        cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(X.shape[1])])
+        assert rel_fro(G.stats_finalize(c).cov, cov) < 2e-6
+        c.close()
+    # two calls: rows [0, 4) through the fragment pass (too few rows for a tensor copy), the
+    # rest through tcgen05; the pivot of the first call serves both
+    X = big
+    blk, _ = block_cols(X)
+    with G.stats_init(G.Config([G.STATS_F32] * 64, G.STATS_BF16X4, [0] * 64)) as c:
+        G.stats_accumulate(c, [blk[j, 0:4] for j in range(64)], 4)
+        G.stats_accumulate(c, [blk[j, 4:X.shape[0]] for j in range(64)], X.shape[0] - 4)
+        cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(64)])
+        assert rel_fro(G.stats_finalize(c).cov, cov) < 2e-6
+
+
 def test_wide_tcgen05_long_paced():
     """Enough 64-row stages per CTA that the units pace one another: against the oracle, and
     chunked into three calls of uneven length (ragged tails inside a stage each time)."""
