@@ -103,25 +103,31 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
-    if (lane == 0) {
-      int s = 0;
-      uint32_t ph = 0;
-      int64_t k = 0;
-      for (; k < my; ++k) {
-        const int64_t st = q0 + k * G;
-        if (k >= kNStages && !wait_live(&f_empty[s], ph ^ 1u, &s_dead)) {
-          record_timeout(&s_dead, P.status);
-          break;
-        }
+    // (the whole warp runs the loop; one lane waits, one elected lane issues)
+    int s = 0;
+    uint32_t ph = 0;
+    int64_t k = 0;
+    for (; k < my; ++k) {
+      const int64_t st = q0 + k * G;
+      const bool ok = __shfl_sync(
+          0xffffffffu, lane == 0 ? (k < kNStages || wait_live(&f_empty[s], ph ^ 1u, &s_dead)) : false, 0);
+      if (!ok) {
+        if (lane == 0) record_timeout(&s_dead, P.status);
+        break;
+      }
+      if (elect_one()) {
         s_rows[s] = static_cast<int>(min(static_cast<int64_t>(kNRows), P.nrows - st * kNRows));
         mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(kNStageBytes));
         tma_load_3d(smem + static_cast<size_t>(s) * kNStageBytes, P.tmap, 0, static_cast<int>(st * kNChunks), 0,
                     &f_full[s]);
-        if (++s == kNStages) {
-          s = 0;
-          ph ^= 1u;
-        }
       }
+      __syncwarp();
+      if (++s == kNStages) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    if (lane == 0) {
       for (int d = 0; d < kNStages && d < k; ++d) {  // no copy in flight at exit
         int sk = s - 1 - d;
         uint32_t pk = ph;
@@ -132,6 +138,7 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         mbar_wait_bounded(&f_full[sk], pk);
       }
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     // The whole warp runs the loop (warp-uniform addresses and descriptors); one elected lane
