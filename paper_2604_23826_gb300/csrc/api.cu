@@ -26,9 +26,11 @@ namespace {
 
 constexpr uint64_t kMagic = 0x3130535441545353ull;  // "SSTATS01"
 constexpr int64_t kDefaultChunkRows = int64_t(1) << 24;
-// In a batch, a 33..64-column table of at least this many rows gets its own tcgen05 launch;
-// smaller ones share the register-fragment launch (one launch costs a few microseconds).
-constexpr int64_t kNarrowBatchMinRows = int64_t(1) << 19;
+// A call on a 33..64-column table of at least this many rows takes the tcgen05 pass; below it
+// the pass's fixed costs (tensor-memory set-up, pipeline fill, per-CTA slots and their merge:
+// tens of microseconds) outweigh its faster streaming.  Batches keep the register-fragment
+// launch, which shares those costs across its tables.
+constexpr int64_t kNarrowMinRows = int64_t(1) << 20;
 
 struct ColPlan {
   int k = 0;         // digit bytes
@@ -652,7 +654,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
     int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
     CK(c, launch_exact(P, c->conv, g, st));
-  } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64 &&
+  } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64 && nrows >= kNarrowMinRows &&
              narrow_eligible(c, dcols, nrows)) {
     stats_status s = run_narrow(c, dcols, nrows, st);
     if (s != STATS_OK) return s;
@@ -1148,10 +1150,7 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
-      if (c->p > 32 && c->p <= 64 && nrows[t] >= kNarrowBatchMinRows && narrow_eligible(c, dcols[t], nrows[t])) {
-        s = run_narrow(c, dcols[t], nrows[t], st);  // large 33..64-column tables: one tcgen05 launch each
-        if (s != STATS_OK) return s;
-      } else if (c->p <= 64) {
+      if (c->p <= 64) {
         g32.push_back({c, dcols[t], nrows[t]});
       } else if (wide_eligible(c, dcols[t], nrows[t])) {
         s = launch_pass(c, dcols[t], nrows[t], st);  // one tcgen05 launch per wide table

@@ -361,12 +361,13 @@ def test_wide_tcgen05_pass(mode, p, n):
 
 
 @pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
-@pytest.mark.parametrize("p,n", [(64, 40_000), (33, 33), (48, 100_003), (64, 32_007), (40, 64 * 77 + 32),
-                                 (64, 1_000_001)])
+@pytest.mark.parametrize("p,n", [(64, (1 << 20) + 7), (33, (1 << 20) + 45), (48, (1 << 20) + 63),
+                                 (40, (1 << 20) + 64 * 77 + 32), (64, 3_000_001)])
 def test_narrow_tcgen05_pass(mode, p, n):
-    """33..64 columns from a [p, ld] block (the tcgen05 pass with h and l stacked into one M = 128
-    operand): against the oracle, and against the register-fragment pass on the same values
-    (separate column allocations)."""
+    """33..64 columns from a [p, ld] block, calls of at least 2^20 rows (the tcgen05 pass with h and
+    l stacked into one M = 128 operand), ragged tails in either 32-row chunk of the last stage:
+    against the oracle, and against the register-fragment pass on the same values (separate
+    column allocations)."""
     X = independent_table(700 + p, n, p)
     blk, cols = block_cols(X)
     raw, an = run_cols(cols, n, mode)
@@ -385,10 +386,10 @@ def test_narrow_tcgen05_pass(mode, p, n):
 
 
 def test_narrow_in_a_batch_and_across_calls():
-    """A batch mixing a large 64-column block (its own tcgen05 launch) with small tables (the shared
-    register-fragment launch); the large table also split into two calls of different paths."""
+    """A batch mixing a large 64-column block with small tables (one register-fragment launch); the
+    large table also split into two calls of different paths (fragment pass, then tcgen05)."""
     rng = np.random.default_rng(8)
-    big = independent_table(801, 600_001, 64)
+    big = independent_table(801, 1_200_001, 64)
     small = [independent_table(810 + t, int(rng.integers(1000, 50_000)), int(rng.choice([8, 40, 64])))
              for t in range(6)]
     tabs = [big] + small
