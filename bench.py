@@ -508,13 +508,15 @@ def run_tables(args, rank: int, world: int, local_rank: int):
             cols = [[x.data_ptr() + 4 * x.stride(0) * j for j in range(x.shape[0])] for x in views]
             tabs = [ctxs[t] for t in g]
             rows = [params[t][0] for t in g]
+            batch = G.BatchArgs(tabs, cols, rows)  # argument arrays, like the pointers, built outside
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             h0 = time.perf_counter()
-            G.stats_accumulate_batched(tabs, cols, rows, stream)
-            host_ms.append((time.perf_counter() - h0) * 1e3)
+            G.stats_accumulate_batched(batch, stream=stream)
+            if record:
+                host_ms.append((time.perf_counter() - h0) * 1e3)
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1)

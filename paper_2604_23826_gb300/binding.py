@@ -8,6 +8,7 @@ no fallback of any kind.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
@@ -231,21 +232,36 @@ def stats_accumulate_host(ctx: Ctx, hcols: Sequence, nrows: int, chunk_rows: int
            "stats_accumulate_host")
 
 
-def stats_accumulate_batched(ctxs: Sequence[Ctx], dcols: Sequence[Sequence], nrows: Sequence[int], stream=None):
-    """Add table t (dcols[t]: its device columns, nrows[t] rows) to ctxs[t], all in one pass."""
+class BatchArgs:
+    """The argument arrays of one stats_accumulate_batched call, built once (the marshalling of
+    thousands of column pointers costs milliseconds in Python) and reusable for later calls on
+    the same contexts and column addresses."""
+
+    def __init__(self, ctxs: Sequence[Ctx], dcols: Sequence[Sequence], nrows: Sequence[int]):
+        n = len(ctxs)
+        self.ctxs = list(ctxs)
+        self.handles = np.fromiter((c.handle.value for c in ctxs), dtype=np.uint64, count=n)
+        if n and dcols[0] and isinstance(dcols[0][0], int):
+            self.flat = np.fromiter(itertools.chain.from_iterable(dcols), dtype=np.uint64)
+        else:
+            self.flat = np.fromiter((_ptr(x) for cols in dcols for x in cols), dtype=np.uint64)
+        counts = np.fromiter((len(cols) for cols in dcols), dtype=np.int64, count=n)
+        starts = np.concatenate(([0], np.cumsum(counts)[:-1])) if n else np.zeros(0, np.int64)
+        # one flat array of column pointers and, per table, the address of its first entry
+        self.outer = (self.flat.ctypes.data + 8 * starts).astype(np.uint64)
+        self.rows = np.asarray(nrows, dtype=np.int64)
+        self.n = n
+
+
+def stats_accumulate_batched(ctxs, dcols: Sequence[Sequence] = None, nrows: Sequence[int] = None, stream=None):
+    """Add table t (dcols[t]: its device columns, nrows[t] rows) to ctxs[t], all in one pass;
+    ctxs may instead be a prepared BatchArgs."""
     L = load()
     L.stats_accumulate_batched.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p]
     L.stats_accumulate_batched.restype = ctypes.c_int
-    n = len(ctxs)
-    handles = np.fromiter((c.handle.value for c in ctxs), dtype=np.uint64, count=n)
-    # one flat array of column pointers and, per table, the address of its first entry
-    flat = np.fromiter((_ptr(x) for cols in dcols for x in cols), dtype=np.uint64)
-    counts = np.fromiter((len(cols) for cols in dcols), dtype=np.int64, count=n)
-    starts = np.concatenate(([0], np.cumsum(counts)[:-1])) if n else np.zeros(0, np.int64)
-    outer = (flat.ctypes.data + 8 * starts).astype(np.uint64)
-    rows = np.asarray(nrows, dtype=np.int64)
-    _check(L.stats_accumulate_batched(handles.ctypes.data, n, outer.ctypes.data, rows.ctypes.data,
+    b = ctxs if isinstance(ctxs, BatchArgs) else BatchArgs(ctxs, dcols, nrows)
+    _check(L.stats_accumulate_batched(b.handles.ctypes.data, b.n, b.outer.ctypes.data, b.rows.ctypes.data,
                                       _stream_handle(stream)), "stats_accumulate_batched")
 
 
