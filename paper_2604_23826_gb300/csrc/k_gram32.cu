@@ -60,10 +60,11 @@ template <int P>
 struct G32 {
   // P >= 32: 240-row stages, filled by one 2D tensor copy when the table's columns are
   // uniformly strided (a 960-byte column stride is free of bank conflicts as it is);
-  // P <= 16: 32 KB stages of per-column bulk copies (2-4 KB each), columns RS + 16 apart
+  // P <= 16: 64 KB stages of per-column bulk copies of 4 KB (P = 16) or 8 KB (P = 8); bulk
+  // copies of 2 KB feed at ~75 % of HBM, 4 KB ones at ~97 %; columns RS + 16 apart
   static constexpr bool TMAP = P >= 32;
-  static constexpr int STAGES = P == 64 ? 3 : P == 32 ? 6 : 4;
-  static constexpr int RS = TMAP ? 240 : 8192 / P;  // rows per stage
+  static constexpr int STAGES = P == 64 ? 3 : P == 32 ? 6 : 3;
+  static constexpr int RS = TMAP ? 240 : 16384 / P;  // rows per stage
   static constexpr int LDC = TMAP ? RS : RS + 16;   // column stride in floats (= 16 mod 32)
   static constexpr int SF = P * LDC;                // floats per stage
   static constexpr int KBS = RS / 16;
