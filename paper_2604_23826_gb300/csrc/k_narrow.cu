@@ -371,46 +371,68 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
   }
 }
 
-// The CTA slots, in CTA order, into the context's double-double accumulators.
+// Sum of slot entry idx over CTAs [q0, q1) into (h, l), eight loads in flight (the entries of
+// consecutive CTAs are 133 KB apart: each load is its own L2 round trip).
+__device__ __forceinline__ void sum_slots(const float2* slots, int idx, int q0, int q1, float& h, float& l) {
+  for (int q = q0; q < q1; q += 8) {
+    float2 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      x[u] = q + u < q1 ? __ldcg(slots + static_cast<size_t>(q + u) * kWideSlotPairs + idx) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      two_sum(h, l, x[u].x);
+      two_sum(h, l, x[u].y);
+    }
+  }
+}
+
+__device__ __forceinline__ void dd_add(double* hi, double* lo, int64_t e, float h, float l) {
+  const double v = static_cast<double>(h) + static_cast<double>(l);
+  const double s = hi[e] + v;
+  const double bp = s - hi[e];
+  lo[e] += (hi[e] - (s - bp)) + (v - bp);
+  hi[e] = s;
+}
+
+// The CTA slots into the context's double-double accumulators.  Block m (< p) takes row m of
+// S, block p the column sums; thread (n, quarter) adds CTAs [quarter G / 4, (quarter + 1) G / 4)
+// and the quarters are then combined in order, so the result depends on the grid only.
 template <bool X4>
-__global__ void __launch_bounds__(64) narrow_merge_kernel(const __grid_constant__ WideParams P, int grid, int parts) {
+__global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant__ WideParams P, int grid) {
+  __shared__ float2 part[4][kNCols];
   const int p = P.p;
   const float2* slots = reinterpret_cast<const float2*>(P.slots);
-  const int n = threadIdx.x;
-  auto add = [&](float& h, float& l, int idx) {
-    for (int q = 0; q < grid; ++q) {
-      const float2 x = __ldcg(slots + static_cast<size_t>(q) * kWideSlotPairs + idx);
-      two_sum(h, l, x.x);
-      two_sum(h, l, x.y);
+  const int n = threadIdx.x & (kNCols - 1), qq = threadIdx.x / kNCols;
+  const int q0 = qq * grid / 4, q1 = (qq + 1) * grid / 4;
+  const int m = blockIdx.x;
+  float h = 0.f, l = 0.f;
+  if (m < p) {
+    if (n >= m && n < p) {
+      const int hm = 16 * (m / 8) + m % 8, hn = 16 * (n / 8) + n % 8;  // operand rows of h(m), h(n)
+      sum_slots(slots, hm * kNSlotStride + n, q0, q1, h, l);          // H^T H (BF16x4: + H^T L)
+      sum_slots(slots, (hm + 8) * kNSlotStride + n, q0, q1, h, l);    // L^T H (BF16x4: + L^T L)
+      if (!X4) {
+        sum_slots(slots, (hn + 8) * kNSlotStride + m, q0, q1, h, l);  // H^T L, from the transposed entry
+        if (n == m) sum_slots(slots, 128 * kNSlotStride + 128 + m, q0, q1, h, l);  // + diag(L^T L)
+      }
     }
-  };
-  for (int m = blockIdx.x; m < p; m += parts) {
-    if (n < m || n >= p) continue;
-    const int hm = 16 * (m / 8) + m % 8, hn = 16 * (n / 8) + n % 8;  // operand rows of h(m), h(n)
-    float h = 0.f, l = 0.f;
-    add(h, l, hm * kNSlotStride + n);          // H^T H (BF16x4: + H^T L)
-    add(h, l, (hm + 8) * kNSlotStride + n);    // L^T H (BF16x4: + L^T L)
-    if (!X4) {
-      add(h, l, (hn + 8) * kNSlotStride + m);  // H^T L, from the transposed entry
-      if (n == m) add(h, l, 128 * kNSlotStride + 128 + m);  // + the diagonal of L^T L
+  } else if (n < p) {
+    sum_slots(slots, 128 * kNSlotStride + n, q0, q1, h, l);  // column sums
+  }
+  part[qq][n] = make_float2(h, l);
+  __syncthreads();
+  if (qq == 0) {
+    for (int k = 1; k < 4; ++k) {
+      two_sum(h, l, part[k][n].x);
+      l += part[k][n].y;
     }
-    const int64_t e = static_cast<int64_t>(m) * p - static_cast<int64_t>(m) * (m - 1) / 2 + (n - m);
-    const double v = static_cast<double>(h) + static_cast<double>(l);
-    const double s = P.acc_S[e] + v;
-    const double bp = s - P.acc_S[e];
-    P.acc_S_lo[e] += (P.acc_S[e] - (s - bp)) + (v - bp);
-    P.acc_S[e] = s;
+    if (m < p && n >= m && n < p)
+      dd_add(P.acc_S, P.acc_S_lo, static_cast<int64_t>(m) * p - static_cast<int64_t>(m) * (m - 1) / 2 + (n - m), h, l);
+    else if (m == p && n < p)
+      dd_add(P.acc_s, P.acc_s_lo, n, h, l);
+    if (m == p && n == 0) *P.acc_n += P.nrows;
   }
-  if (blockIdx.x == 0 && n < p) {  // column sums
-    float h = 0.f, l = 0.f;
-    add(h, l, 128 * kNSlotStride + n);
-    const double v = static_cast<double>(h) + static_cast<double>(l);
-    const double s = P.acc_s[n] + v;
-    const double bp = s - P.acc_s[n];
-    P.acc_s_lo[n] += (P.acc_s[n] - (s - bp)) + (v - bp);
-    P.acc_s[n] = s;
-  }
-  if (blockIdx.x == 0 && n == 0) *P.acc_n += P.nrows;
 }
 
 template <bool X4>
@@ -421,8 +443,7 @@ cudaError_t launch_n(const WideParams& P, int grid, cudaStream_t st) {
   narrow_kernel<X4><<<grid, kNThreads, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int parts = 32;
-  narrow_merge_kernel<X4><<<parts, 64, 0, st>>>(P, grid, parts);
+  narrow_merge_kernel<X4><<<P.p + 1, 256, 0, st>>>(P, grid);
   return cudaGetLastError();
 }
 

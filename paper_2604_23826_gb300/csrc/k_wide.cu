@@ -442,68 +442,83 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
   }
 }
 
-// The units' CTA slots, in CTA order, into the context's double-double accumulators.
-// Block (unit, part) takes rows part, part + parts, ... of the unit's 128 x 128 block.
+// Sum of slot entry idx over CTAs [q0, q1) into (h, l), eight loads in flight (the entries of
+// consecutive CTAs are 133 KB apart: each load is its own L2 round trip).
+__device__ __forceinline__ void sum_slots(const float2* slots, int idx, int q0, int q1, float& h, float& l) {
+  for (int q = q0; q < q1; q += 8) {
+    float2 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      x[u] = q + u < q1 ? __ldcg(slots + static_cast<size_t>(q + u) * kWideSlotPairs + idx) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      two_sum(h, l, x[u].x);
+      two_sum(h, l, x[u].y);
+    }
+  }
+}
+
+__device__ __forceinline__ void dd_add(double* hi, double* lo, int64_t e, float h, float l) {
+  const double v = static_cast<double>(h) + static_cast<double>(l);
+  const double s = hi[e] + v;
+  const double bp = s - hi[e];
+  lo[e] += (hi[e] - (s - bp)) + (v - bp);
+  hi[e] = s;
+}
+
+// The units' CTA slots into the context's double-double accumulators.  Block (m, unit) takes
+// row m of the unit's 128 x 128 block (m = 128: a diagonal unit's column sums); thread
+// (n, quarter) adds a quarter of the unit's CTAs, and the quarters are combined in order, so
+// the result depends on the grid only.
 template <bool X4>
-__global__ void __launch_bounds__(128) wide_merge_kernel(const __grid_constant__ WideParams P, int parts) {
-  const int unit = blockIdx.x / parts, part = blockIdx.x % parts;
+__global__ void __launch_bounds__(512) wide_merge_kernel(const __grid_constant__ WideParams P) {
+  __shared__ float4 part[4][kWBlk];
+  const int unit = blockIdx.y, m = blockIdx.x;
   const int I = P.unit_i[unit], J = P.unit_j[unit];
   const int first = P.unit_first[unit], G = P.unit_ctas[unit];
+  const int n = threadIdx.x & (kWBlk - 1), qq = threadIdx.x / kWBlk;
+  const int q0 = first + qq * G / 4, q1 = first + (qq + 1) * G / 4;
   const int p = P.p;
   const float2* slots = reinterpret_cast<const float2*>(P.slots);
-  for (int m = part; m < kWBlk; m += parts) {
-    const int row = I * kWBlk + m;
-    if (row >= p) break;
-    const int n = threadIdx.x;
-    const int col = J * kWBlk + n;
-    if (col < row || col >= p) continue;
-    float h = 0.f, l = 0.f;
-    for (int q = 0; q < G; ++q) {
-      const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + m * kWBlk + n);
-      two_sum(h, l, x.x);
-      two_sum(h, l, x.y);
+  const int row = I * kWBlk + m, col = J * kWBlk + n;
+  const bool two_l = !X4 && I == J;  // BF16x3 diagonal unit: the block holds H^T H + 2 H^T L
+  bool active;
+  float h = 0.f, l = 0.f, qh = 0.f, ql = 0.f;
+  if (m < kWBlk) {
+    active = row < p && col >= row && col < p;
+    if (active) {
+      sum_slots(slots, m * kWBlk + n, q0, q1, h, l);
+      if (two_l) sum_slots(slots, n * kWBlk + m, q0, q1, h, l);  // S = (D + D^T) / 2
+      if (!X4 && col == row) sum_slots(slots, kWBlk * kWBlk + kWBlk + m, q0, q1, qh, ql);  // + diag(L^T L)
     }
-    if (!X4 && I == J) {
-      // BF16x3 diagonal unit: the block holds D = H^T H + 2 H^T L; S = (D + D^T) / 2
-      for (int q = 0; q < G; ++q) {
-        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + n * kWBlk + m);
-        two_sum(h, l, x.x);
-        two_sum(h, l, x.y);
-      }
-      h *= 0.5f;
-      l *= 0.5f;
-    }
-    if (!X4 && col == row) {  // BF16x3: + the diagonal of L^T L
-      for (int q = 0; q < G; ++q) {
-        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + kWBlk * kWBlk + kWBlk + m);
-        two_sum(h, l, x.x);
-        two_sum(h, l, x.y);
-      }
-    }
-    const int64_t e = static_cast<int64_t>(row) * p - static_cast<int64_t>(row) * (row - 1) / 2 + (col - row);
-    const double v = static_cast<double>(h) + static_cast<double>(l);
-    const double s = P.acc_S[e] + v;
-    const double bp = s - P.acc_S[e];
-    P.acc_S_lo[e] += (P.acc_S[e] - (s - bp)) + (v - bp);
-    P.acc_S[e] = s;
+  } else {
+    active = I == J && col < p;
+    if (active) sum_slots(slots, kWBlk * kWBlk + n, q0, q1, h, l);  // column sums
   }
-  if (I == J && part == 0) {  // column sums of the block
-    const int c = threadIdx.x, col = I * kWBlk + c;
-    if (col < p) {
-      float h = 0.f, l = 0.f;
-      for (int q = 0; q < G; ++q) {
-        const float2 x = __ldcg(slots + static_cast<size_t>(first + q) * kWideSlotPairs + kWBlk * kWBlk + c);
-        two_sum(h, l, x.x);
-        two_sum(h, l, x.y);
+  part[qq][n] = make_float4(h, l, qh, ql);
+  __syncthreads();
+  if (qq == 0 && active) {
+    for (int k = 1; k < 4; ++k) {
+      const float4 o = part[k][n];
+      two_sum(h, l, o.x);
+      l += o.y;
+      two_sum(qh, ql, o.z);
+      ql += o.w;
+    }
+    if (m < kWBlk) {
+      if (two_l) {
+        h *= 0.5f;
+        l *= 0.5f;
       }
-      const double v = static_cast<double>(h) + static_cast<double>(l);
-      const double s = P.acc_s[col] + v;
-      const double bp = s - P.acc_s[col];
-      P.acc_s_lo[col] += (P.acc_s[col] - (s - bp)) + (v - bp);
-      P.acc_s[col] = s;
+      two_sum(h, l, qh);
+      l += ql;
+      dd_add(P.acc_S, P.acc_S_lo, static_cast<int64_t>(row) * p - static_cast<int64_t>(row) * (row - 1) / 2 + (col - row),
+             h, l);
+    } else {
+      dd_add(P.acc_s, P.acc_s_lo, col, h, l);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *P.acc_n += P.nrows;
+  if (unit == 0 && m == 0 && threadIdx.x == 0) *P.acc_n += P.nrows;
 }
 
 template <bool X4>
@@ -512,8 +527,7 @@ cudaError_t launch_w(const WideParams& P, int grid, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(wide_kernel<X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   wide_kernel<X4><<<grid, kWThreads, smem, st>>>(P);
-  const int parts = 16;
-  wide_merge_kernel<X4><<<P.nunits * parts, 128, 0, st>>>(P, parts);
+  wide_merge_kernel<X4><<<dim3(kWBlk + 1, P.nunits), 512, 0, st>>>(P);
   return cudaGetLastError();
 }
 
