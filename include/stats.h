@@ -211,6 +211,27 @@ stats_status stats_raw(stats_ctx* ctx, int64_t* n, double* s, double* S_upper, s
 stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals, double* evecs,
                             int32_t pca_on);
 
+/* Streaming analysis (finalize after every chunk of a growing table): stats_finalize with
+ * the eigen-solver seeded by an earlier result.  The paper's method re-derives every
+ * quantity from (n, s, S) alone ("Data Representation and Sufficient Statistics"), so a
+ * snapshot can be taken between any two accumulate calls; this call makes a snapshot's
+ * PCA ("Principal Component Analysis Results") cheap when the matrix has moved little.
+ *   evecs_prev: HOST, p_a*p_a doubles, row k = eigenvector k, as written by an earlier
+ *     stats_finalize / stats_finalize_warm (any ctx with the same p_a), or NULL (cold
+ *     start).  The matrix M (cov, or corr with pca_on = 1) is rotated into that basis,
+ *     V^T M V, before the cyclic Jacobi sweeps.  A seed whose columns are not orthonormal
+ *     (max |V^T V - I| > 1e-9, or NaN) is ignored.  The eigenpairs are those of M
+ *     whatever the seed, up to rounding; inside a cluster of equal eigenvalues the
+ *     eigenvectors may be another basis of the same subspace.
+ *   sweeps: may be NULL; receives the number of Jacobi sweeps taken, -1 when no
+ *     eigenpairs were computed.
+ * The other arguments are those of stats_finalize.  With more than 23 analysis columns,
+ * or with a seed, the eigen-solver is a cooperative launch over the GPU's SMs.
+ * Errors: those of stats_finalize; ETIMEOUT when a grid-wide wait of the eigen-solver
+ * ran out (after 2 s; the ctx stays usable, the eigenpairs are not written). */
+stats_status stats_finalize_warm(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals,
+                                 double* evecs, int32_t pca_on, const double* evecs_prev, int32_t* sweeps);
+
 /* stats_finalize for many contexts in one launch (one thread block per context; the
  * FP64 eigen-solver of each block is what a single call costs, so many contexts cost
  * about one call per SM-load instead of one call each).  Synchronises every context.

@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
     L.stats_raw.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I128), ctypes.POINTER(_I128)]
     L.stats_finalize.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 5 + [i32]
+    L.stats_finalize_warm.argtypes = [vp] + [ctypes.POINTER(ctypes.c_double)] * 5 + [i32, vp, ctypes.POINTER(i32)]
     L.stats_export.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     L.stats_import.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_size_t]
     L.stats_destroy.argtypes = [vp]
@@ -103,7 +104,7 @@ def load() -> ctypes.CDLL:
     L.stats_file_check_table1.argtypes = [cp, ctypes.c_uint64, ctypes.c_uint64, i32, i64, ctypes.POINTER(i64)]
     L.stats_accumulate_file.argtypes = [vp, cp, i64, i64, i64, vp]
     for name in ("stats_init", "stats_accumulate", "stats_accumulate_host", "stats_merge", "stats_sync",
-                 "stats_reset", "stats_raw", "stats_finalize", "stats_export", "stats_import", "stats_set_grid",
+                 "stats_reset", "stats_raw", "stats_finalize", "stats_finalize_warm", "stats_export", "stats_import", "stats_set_grid",
                  "stats_table1_config", "stats_gen_table1", "stats_file_write", "stats_file_write_table1",
                  "stats_file_info", "stats_file_read_rows", "stats_file_check_table1", "stats_accumulate_file"):
         getattr(L, name).restype = ctypes.c_int
@@ -336,6 +337,7 @@ class Analysis:
     corr: np.ndarray
     evals: np.ndarray
     evecs: np.ndarray   # row k = eigenvector k
+    sweeps: int = -1    # Jacobi sweeps taken (stats_finalize_warm only; -1: not reported)
 
 
 def stats_finalize(ctx: Ctx, pca_on: int = 0) -> Analysis:
@@ -348,6 +350,56 @@ def stats_finalize(ctx: Ctx, pca_on: int = 0) -> Analysis:
     dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
     _check(load().stats_finalize(ctx.handle, dp(mean), dp(cov), dp(corr), dp(ev), dp(V), pca_on), "stats_finalize")
     return Analysis(mean, cov, corr, ev, V)
+
+
+def stats_finalize_warm(ctx: Ctx, pca_on: int = 0, evecs_prev=None) -> Analysis:
+    """stats_finalize with the eigen-solver seeded by evecs_prev (rows = eigenvectors, e.g. the
+    evecs of an earlier snapshot), or cold when None; the result carries the sweep count."""
+    pa = stats_num_analysis_columns(ctx)
+    mean = np.zeros(pa)
+    cov = np.zeros((pa, pa))
+    corr = np.zeros((pa, pa))
+    ev = np.zeros(pa)
+    V = np.zeros((pa, pa))
+    sw = ctypes.c_int32(-1)
+    seed = None
+    if evecs_prev is not None:
+        seed = np.ascontiguousarray(evecs_prev, dtype=np.float64)
+        if seed.shape != (pa, pa):
+            raise ValueError(f"evecs_prev must be {pa} x {pa}")
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    _check(load().stats_finalize_warm(ctx.handle, dp(mean), dp(cov), dp(corr), dp(ev), dp(V), pca_on,
+                                      None if seed is None else seed.ctypes.data, ctypes.byref(sw)),
+           "stats_finalize_warm")
+    return Analysis(mean, cov, corr, ev, V, int(sw.value))
+
+
+class StreamingAnalysis:
+    """Snapshots of a growing table: accumulate chunks with update(), and after any of them
+    take snapshot(), whose eigen-solve is seeded by the previous snapshot's eigenvectors."""
+
+    def __init__(self, cfg: "Config", pca_on: int = 0):
+        self.ctx = stats_init(cfg)
+        self.pca_on = pca_on
+        self.prev = None
+
+    def update(self, dcols: Sequence, nrows: int, stream=None):
+        stats_accumulate(self.ctx, dcols, nrows, stream)
+
+    def snapshot(self) -> Analysis:
+        an = stats_finalize_warm(self.ctx, self.pca_on, self.prev)
+        if np.all(np.isfinite(an.evecs)):
+            self.prev = an.evecs
+        return an
+
+    def close(self):
+        self.ctx.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def stats_finalize_batched(ctxs: Sequence[Ctx], pca_on: int = 0) -> list:

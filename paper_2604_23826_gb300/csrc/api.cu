@@ -92,6 +92,8 @@ struct stats_ctx {
   bool shift_set = false;
   double* d_out = nullptr;              // finalize result
   double* d_work = nullptr;             // finalize scratch
+  double* d_jac = nullptr;              // grid-wide eigen-solver scratch (allocated on first use)
+  int coop = 0;                         // the device takes cooperative launches
   double* h_out = nullptr;              // pinned host copy of the result
   FinalLayout lay{};
   // host streaming
@@ -799,13 +801,50 @@ void build_final_params(const stats_ctx* c, int want_pca, int pca_on, FinalParam
   F.work = c->d_work;
 }
 
-stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on) {
+// From this many analysis columns on, the eigen-solver runs over the whole GPU
+// (jacobi_grid_kernel) instead of inside the one-block finalize kernel: GB300 has
+// about 2 FP64 FMAs per SM clock, so one block is far too slow for p_a in the hundreds.
+constexpr int kGridJacobiMinColumns = 24;
+
+// Finalize on the ctx's stream.  With want_pca, the eigen-decomposition runs either in the
+// finalize kernel (small p_a) or in the grid-wide solver, seeded by `seed` (host, p_a x p_a,
+// rows = eigenvectors) when given.  Synchronises.
+stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on, const double* seed = nullptr) {
   FinalParams F;
   build_final_params(c, want_pca, pca_on, F);
   cudaStream_t st = c->last;
+  const int pa = c->pa;
+  const int grid = (want_pca && c->coop && pa >= 2 && (pa >= kGridJacobiMinColumns || seed)) ? jacobi_grid_blocks(pa, c->sms) : 0;
+  JacobiParams J{};
+  if (grid > 0) {
+    if (!c->d_jac) CK(c, cudaMalloc(&c->d_jac, jacobi_scratch_doubles(pa) * sizeof(double)));
+    const size_t m = pa + (pa & 1);
+    J.a = c->d_jac;
+    J.b = J.a + m * m;
+    J.v = J.b + m * m;
+    J.w = J.v + m * m;
+    double* basis = J.w + m * m;
+    J.slots = basis + static_cast<size_t>(pa) * pa;
+    J.bar = reinterpret_cast<unsigned int*>(J.slots + 1024);
+    J.ctl = reinterpret_cast<const int32_t*>(J.bar + 4);
+    J.basis = seed ? basis : nullptr;
+    J.out = c->d_out;
+    J.evals_off = c->lay.evals;
+    J.evecs_off = c->lay.evecs;
+    J.flags_off = c->lay.flags;
+    J.pa = pa;
+    J.m = static_cast<int32_t>(m);
+    F.defer_A = J.a;
+    F.defer_ctl = const_cast<int32_t*>(J.ctl);
+    F.defer_m = J.m;
+    if (seed) CK(c, cudaMemcpyAsync(basis, seed, sizeof(double) * pa * pa, cudaMemcpyHostToDevice, st));
+    CK(c, cudaMemsetAsync(J.bar, 0, 8 * sizeof(unsigned int), st));
+  }
   CK(c, launch_finalize(F, st));
+  if (grid > 0) CK(c, launch_jacobi_grid(J, grid, st));
   CK(c, cudaMemcpyAsync(c->h_out, c->d_out, c->lay.total * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(c, cudaStreamSynchronize(st));
+  if (c->h_out[c->lay.flags + 5] != 0.0) return STATS_ETIMEOUT;
   return STATS_OK;
 }
 
@@ -822,6 +861,7 @@ void free_ctx(stats_ctx* c) {
   cudaFree(c->d_tmap);
   cudaFree(c->d_out);
   cudaFree(c->d_work);
+  cudaFree(c->d_jac);
   if (c->h_out) cudaFreeHost(c->h_out);
   for (int b = 0; b < 2; ++b) {
     cudaFree(c->d_stage[b]);
@@ -869,6 +909,7 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
   }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->sms < 1) c->sms = 1;
+  cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, c->device);
 
   stats_status s = STATS_OK;
   if (c->mode == STATS_EXACT) {
@@ -1376,6 +1417,12 @@ stats_status stats_raw(stats_ctx* ctx, int64_t* n, double* s, double* S_upper, s
 
 stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals, double* evecs,
                             int32_t pca_on) {
+  return stats_finalize_warm(ctx, mean, cov, corr, evals, evecs, pca_on, nullptr, nullptr);
+}
+
+stats_status stats_finalize_warm(stats_ctx* ctx, double* mean, double* cov, double* corr, double* evals,
+                                 double* evecs, int32_t pca_on, const double* evecs_prev, int32_t* sweeps) {
+  if (sweeps) *sweeps = -1;
   stats_status st = stats_sync(ctx);
   if (st != STATS_OK) return st;
   if (pca_on != 0 && pca_on != 1) return STATS_EINVAL;
@@ -1387,11 +1434,12 @@ stats_status stats_finalize(stats_ctx* ctx, double* mean, double* cov, double* c
     CK(ctx, cudaMemcpy(&n, ctx->d_fn, sizeof(n), cudaMemcpyDeviceToHost));
   }
   if (n < 2) return STATS_EINVAL;
-  st = run_finalize(ctx, (evals || evecs) ? 1 : 0, pca_on);
+  st = run_finalize(ctx, (evals || evecs) ? 1 : 0, pca_on, (evals || evecs) ? evecs_prev : nullptr);
   if (st != STATS_OK) return st;
   const FinalLayout& L = ctx->lay;
   const double* h = ctx->h_out;
   const size_t pa = ctx->pa;
+  if (sweeps && h[L.flags + 3] != 0.0) *sweeps = static_cast<int32_t>(h[L.flags + 2]);
   if (mean) memcpy(mean, h + L.mean, sizeof(double) * pa);
   if (cov) memcpy(cov, h + L.cov, sizeof(double) * pa * pa);
   if (corr) memcpy(corr, h + L.corr, sizeof(double) * pa * pa);

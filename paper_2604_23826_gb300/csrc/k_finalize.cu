@@ -426,10 +426,21 @@ __device__ void finalize_body(const FinalParams& P) {
     flags[1] = s_zero;
     flags[2] = 0.0;
     flags[3] = 0.0;
+    flags[5] = 0.0;
+    flags[6] = 0.0;
   }
   __syncthreads();
   const bool pca_ok = P.want_pca && pa > 0 && n_d >= 2.0 && !(P.pca_on == 1 && s_zero > 0);
-  if (pca_ok) {
+  if (P.defer_ctl && tid == 0) *P.defer_ctl = pca_ok ? 1 : 0;
+  if (pca_ok && P.defer_A) {
+    // the grid-wide solver takes over: the matrix, zero-padded to even order m
+    const int m = P.defer_m;
+    const double* src = P.pca_on ? corr : cov;
+    for (int i = tid; i < m * m; i += blockDim.x) {
+      const int r = i / m, c = i % m;
+      P.defer_A[i] = (r < pa && c < pa) ? src[r * pa + c] : 0.0;
+    }
+  } else if (pca_ok) {
     double* A = P.work;
     double* V = P.work + static_cast<size_t>(pa) * pa;
     const double* src = P.pca_on ? corr : cov;
@@ -463,6 +474,402 @@ cudaError_t launch_finalize_batched(const FinalParams* d_params, int count, cuda
 cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream) {
   finalize_kernel<<<1, kThreads, 0, stream>>>(P);
   return cudaGetLastError();
+}
+
+// ------------------------------- Jacobi over the whole GPU -------------------------------
+// One rotation of the round-robin ordering, on the even order m: in round r, pair 0 is
+// (r, m - 1) and pair i > 0 is ((r + i) mod (m - 1), (r - i) mod (m - 1)), sorted.  Every index
+// occurs in exactly one pair, so a round's rotations commute and A' = J^T A J splits into
+// independent 2 x 2 blocks (pair i's rows, pair j's columns).
+namespace {
+
+constexpr int kJacThreads = 256;
+constexpr int kJacMaxItems = 4;                       // work items per thread and round
+constexpr unsigned long long kGridWaitNs = 2000000000ull;  // a grid-wide wait gives up after 2 s
+
+__device__ __forceinline__ void pair_of(int r, int i, int m, int& p, int& q) {
+  if (i == 0) {
+    p = r;
+    q = m - 1;
+  } else {
+    p = (r + i) % (m - 1);
+    q = (r - i + (m - 1)) % (m - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* a) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of each block publishes the block's
+// writes (fence), arrives, and the last arrival resets the count and advances the
+// generation; the others poll the generation.  A poll that outlasts kGridWaitNs sets the
+// shared error word; a block that sees it set leaves.  Returns false in every block once
+// the error is set.
+__device__ bool grid_sync(unsigned int* bar, unsigned int& gen, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar[0], 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], g + 1);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(&bar[1]) == g) {
+        if (ld_acquire_u32(&bar[2]) != 0u) break;
+        if (global_ns() - t0 > kGridWaitNs) {
+          atomicExch(&bar[2], 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ld_acquire_u32(&bar[2]) != 0u) ok = 0;
+    gen = g + 1;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// deterministic block sum (fixed shuffle tree, warps added in order); result valid in thread 0
+__device__ double block_sum(double v, double* s_red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kJacThreads / 32; ++w) t += s_red[w];
+  __syncthreads();
+  return t;
+}
+
+// Z = op(X) Y for m x m row-major matrices (op(X) = X, or X^T when xt), 16 x 16 tiles shared
+// out over the grid.
+__device__ void grid_matmul(const double* X, const double* Y, double* Z, int m, bool xt, double (*sx)[17],
+                            double (*sy)[17]) {
+  const int nt = (m + 15) / 16;
+  const int r = threadIdx.x / 16, c = threadIdx.x % 16;
+  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const int gi = (t / nt) * 16 + r, gj = (t % nt) * 16 + c;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < m; k0 += 16) {
+      const int gk = k0 + c;
+      const int ri = (t / nt) * 16 + r;
+      sx[r][c] = (ri < m && gk < m) ? (xt ? __ldcg(X + static_cast<size_t>(gk) * m + ri)
+                                          : __ldcg(X + static_cast<size_t>(ri) * m + gk))
+                                    : 0.0;
+      const int rk = k0 + r;
+      sy[r][c] = (rk < m && gj < m) ? __ldcg(Y + static_cast<size_t>(rk) * m + gj) : 0.0;
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) acc = fma(sx[r][kk], sy[kk][c], acc);
+      __syncthreads();
+    }
+    if (gi < m && gj < m) __stcg(Z + static_cast<size_t>(gi) * m + gj, acc);
+  }
+}
+
+}  // namespace
+
+size_t jacobi_scratch_doubles(int pa) {
+  const size_t m = pa + (pa & 1);
+  return 4 * m * m + static_cast<size_t>(pa) * pa + 1024 + 8;
+}
+
+int jacobi_grid_blocks(int pa, int sms) {
+  const int m = pa + (pa & 1), h = m / 2;
+  const int items = h * h + pa * h;
+  int g = (items + kJacThreads - 1) / kJacThreads;
+  if (g > sms) g = sms;
+  if (g > 512) g = 512;  // two partial sums per block fit the 1024-double slot area
+  if (g < 1) g = 1;
+  if (static_cast<int64_t>(g) * kJacThreads * kJacMaxItems < items) return 0;
+  return g;
+}
+
+__global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __grid_constant__ JacobiParams J) {
+  __shared__ double s_c[128], s_s[128];
+  __shared__ double s_red[kJacThreads / 32];
+  __shared__ double s_x[16][17], s_y[16][17];
+  __shared__ double s_d[256];
+  __shared__ int s_order[256];
+  __shared__ double s_bv[kJacThreads / 32];
+  __shared__ int s_bi[kJacThreads / 32];
+  __shared__ double s_val;
+  __shared__ int s_ok;
+  if (__ldcg(J.ctl) == 0) return;  // the finalize kernel found the eigenpairs undefined
+  const int tid = threadIdx.x;
+  const int pa = J.pa, m = J.m, h = m / 2;
+  const int nthreads = gridDim.x * kJacThreads;
+  const int gtid = blockIdx.x * kJacThreads + tid;
+  unsigned int gen = 0;
+  bool seeded = false;
+  double* A = J.a;
+  double* B = J.b;
+  double* V = J.v;
+  double* flags = J.out + J.flags_off;
+
+  // V = I, or the previous eigenvectors as columns
+  for (int i = gtid; i < m * m; i += nthreads) {
+    const int r = i / m, c = i % m;
+    double v = (r == c) ? 1.0 : 0.0;
+    if (J.basis && r < pa && c < pa) v = J.basis[static_cast<size_t>(c) * pa + r];
+    __stcg(V + i, v);
+  }
+  if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+  if (J.basis) {
+    // the seed is used only if its columns are orthonormal: max |V^T V - I| <= 1e-9
+    grid_matmul(V, V, J.w, m, true, s_x, s_y);
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    double dev = 0.0;
+    for (int i = gtid; i < m * m; i += nthreads) {
+      const double x = __ldcg(J.w + i) - ((i / m == i % m) ? 1.0 : 0.0);
+      dev = fmax(dev, x != x ? 1.0 : fabs(x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = dev;
+    __syncthreads();
+    if (tid == 0) {
+      double d = 0.0;
+      for (int w = 0; w < kJacThreads / 32; ++w) d = fmax(d, s_red[w]);
+      __stcg(J.slots + blockIdx.x, d);
+    }
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (tid == 0) {
+      double d = 0.0;
+      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) d = fmax(d, __ldcg(J.slots + b));
+      s_val = d;
+    }
+    __syncthreads();
+    seeded = s_val <= 1e-9;
+    __syncthreads();
+    if (!seeded) {  // cold start after all
+      for (int i = gtid; i < m * m; i += nthreads) __stcg(V + i, (i / m == i % m) ? 1.0 : 0.0);
+      if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    }
+  }
+  if (seeded) {
+    // A <- V^T A V, symmetrised: W = A V, B = V^T W, A = (B + B^T) / 2
+    grid_matmul(A, V, J.w, m, false, s_x, s_y);
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    grid_matmul(V, J.w, B, m, true, s_x, s_y);
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    for (int i = gtid; i < m * m; i += nthreads) {
+      const int r = i / m, c = i % m;
+      __stcg(A + i, 0.5 * (__ldcg(B + static_cast<size_t>(r) * m + c) + __ldcg(B + static_cast<size_t>(c) * m + r)));
+    }
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+  }
+  {
+    // ||A||_F^2 once; the off-diagonal part before every sweep
+    double lf = 0.0, lo = 0.0;
+    for (int i = gtid; i < m * m; i += nthreads) {
+      const double x = __ldcg(A + i);
+      lf += x * x;
+      if (i / m != i % m) lo += x * x;
+    }
+    const double bf = block_sum(lf, s_red);
+    const double bo = block_sum(lo, s_red);
+    if (tid == 0) {
+      __stcg(J.slots + blockIdx.x, bf);
+      __stcg(J.slots + gridDim.x + blockIdx.x, bo);
+    }
+    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (tid == 0) {
+      double t = 0.0;
+      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) t += __ldcg(J.slots + b);
+      s_val = t;
+    }
+    __syncthreads();
+    const double fro2 = s_val;
+    __syncthreads();
+    const int nA = h * h, nItems = h * h + pa * h;
+    int sweep = 0;
+    for (; sweep < 60; ++sweep) {
+      if (tid == 0) {
+        double t = 0.0;
+        for (int b = 0; b < static_cast<int>(gridDim.x); ++b) t += __ldcg(J.slots + gridDim.x + b);
+        s_val = t;
+      }
+      __syncthreads();
+      const double off = s_val;
+      __syncthreads();
+      if (off == 0.0 || off <= 1e-34 * fro2) break;
+      for (int round = 0; round < m - 1; ++round) {
+        // this thread's items: loads first, so their latency overlaps the angle computation
+        double x0[kJacMaxItems], x1[kJacMaxItems], x2[kJacMaxItems], x3[kJacMaxItems];
+#pragma unroll
+        for (int u = 0; u < kJacMaxItems; ++u) {
+          const int it = gtid + u * nthreads;
+          x0[u] = x1[u] = x2[u] = x3[u] = 0.0;
+          if (it < nA) {
+            int pi, qi, pj, qj;
+            pair_of(round, it / h, m, pi, qi);
+            pair_of(round, it % h, m, pj, qj);
+            x0[u] = __ldcg(A + static_cast<size_t>(pi) * m + pj);
+            x1[u] = __ldcg(A + static_cast<size_t>(pi) * m + qj);
+            x2[u] = __ldcg(A + static_cast<size_t>(qi) * m + pj);
+            x3[u] = __ldcg(A + static_cast<size_t>(qi) * m + qj);
+          } else if (it < nItems) {
+            const int k = (it - nA) / h;
+            int pj, qj;
+            pair_of(round, (it - nA) % h, m, pj, qj);
+            x0[u] = __ldcg(V + static_cast<size_t>(k) * m + pj);
+            x1[u] = __ldcg(V + static_cast<size_t>(k) * m + qj);
+          }
+        }
+        // rotation angles of this round, from A (every block derives all of them)
+        for (int i = tid; i < h; i += kJacThreads) {
+          int p, q;
+          pair_of(round, i, m, p, q);
+          double c = 1.0, s = 0.0;
+          if (q < pa) {
+            // three independent loads in flight at once
+            const double apq = __ldcg(A + static_cast<size_t>(p) * m + q);
+            const double app = __ldcg(A + static_cast<size_t>(p) * m + p);
+            const double aqq = __ldcg(A + static_cast<size_t>(q) * m + q);
+            if (apq != 0.0) {
+              const double theta = (aqq - app) / (2.0 * apq);
+              const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              s = t * c;
+            }
+          }
+          s_c[i] = c;
+          s_s[i] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kJacMaxItems; ++u) {
+          const int it = gtid + u * nthreads;
+          if (it < nA) {
+            const int i = it / h, j = it % h;
+            int pi, qi, pj, qj;
+            pair_of(round, i, m, pi, qi);
+            pair_of(round, j, m, pj, qj);
+            const double ci = s_c[i], si = s_s[i], cj = s_c[j], sj = s_s[j];
+            // rows (pi, qi), then columns (pj, qj)
+            const double r0 = ci * x0[u] - si * x2[u], r2 = si * x0[u] + ci * x2[u];
+            const double r1 = ci * x1[u] - si * x3[u], r3 = si * x1[u] + ci * x3[u];
+            double y0 = cj * r0 - sj * r1, y1 = sj * r0 + cj * r1;
+            double y2 = cj * r2 - sj * r3, y3 = sj * r2 + cj * r3;
+            if (i == j) y1 = y2 = 0.0;  // the rotated pair's off-diagonal entry is zero by construction
+            __stcg(B + static_cast<size_t>(pi) * m + pj, y0);
+            __stcg(B + static_cast<size_t>(pi) * m + qj, y1);
+            __stcg(B + static_cast<size_t>(qi) * m + pj, y2);
+            __stcg(B + static_cast<size_t>(qi) * m + qj, y3);
+          } else if (it < nItems) {
+            const int k = (it - nA) / h, j = (it - nA) % h;
+            int pj, qj;
+            pair_of(round, j, m, pj, qj);
+            const double cj = s_c[j], sj = s_s[j];
+            __stcg(V + static_cast<size_t>(k) * m + pj, cj * x0[u] - sj * x1[u]);
+            __stcg(V + static_cast<size_t>(k) * m + qj, sj * x0[u] + cj * x1[u]);
+          }
+        }
+        double* t = A;
+        A = B;
+        B = t;
+        if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+      }
+      double lo2 = 0.0;
+      for (int i = gtid; i < m * m; i += nthreads) {
+        const double x = __ldcg(A + i);
+        if (i / m != i % m) lo2 += x * x;
+      }
+      const double bo2 = block_sum(lo2, s_red);
+      if (tid == 0) __stcg(J.slots + gridDim.x + blockIdx.x, bo2);
+      if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    }
+    // descending order (ties by index), eigenvector signs: largest-magnitude component positive
+    for (int c = tid; c < pa; c += kJacThreads) {
+      s_d[c] = __ldcg(A + static_cast<size_t>(c) * m + c);
+      s_order[c] = c;  // stays a valid index even if NaNs leave ranks unassigned
+    }
+    __syncthreads();
+    for (int c = tid; c < pa; c += kJacThreads) {
+      int rank = 0;
+      for (int d = 0; d < pa; ++d) rank += (s_d[d] > s_d[c] || (s_d[d] == s_d[c] && d < c)) ? 1 : 0;
+      s_order[rank] = c;
+    }
+    __syncthreads();
+    double* evals = J.out + J.evals_off;
+    double* evecs = J.out + J.evecs_off;
+    for (int k = blockIdx.x; k < pa; k += gridDim.x) {
+      const int col = s_order[k];
+      double best = -1.0;
+      int bi = 0;
+      double vi = 0.0;
+      if (tid < pa) {
+        vi = __ldcg(V + static_cast<size_t>(tid) * m + col);
+        best = fabs(vi);
+        bi = tid;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if ((tid & 31) == 0) {
+        s_bv[tid >> 5] = best;
+        s_bi[tid >> 5] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double bb = s_bv[0];
+        int ii = s_bi[0];
+        for (int w = 1; w < kJacThreads / 32; ++w)
+          if (s_bv[w] > bb || (s_bv[w] == bb && s_bi[w] < ii)) {
+            bb = s_bv[w];
+            ii = s_bi[w];
+          }
+        s_val = __ldcg(V + static_cast<size_t>(ii) * m + col) < 0.0 ? -1.0 : 1.0;
+        evals[k] = s_d[col];
+      }
+      __syncthreads();
+      if (tid < pa) evecs[static_cast<size_t>(k) * pa + tid] = s_val * vi;
+      __syncthreads();
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+      flags[2] = sweep;
+      flags[3] = 1.0;
+      flags[6] = seeded ? 1.0 : 0.0;
+    }
+  }
+  return;
+timed_out:
+  if (tid == 0) flags[5] = 1.0;
+}
+
+cudaError_t launch_jacobi_grid(const JacobiParams& J, int grid, cudaStream_t stream) {
+  if (grid < 1 || J.m > 256 || J.m < 2) return cudaErrorInvalidValue;
+  void* args[] = {const_cast<JacobiParams*>(&J)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_grid_kernel), dim3(grid), dim3(kJacThreads),
+                                     args, 0, stream);
 }
 
 }  // namespace ss

@@ -254,6 +254,12 @@ struct FinalParams {
   const double* shift;         // FP64 shifted: shift vector or nullptr
   double* out;                 // device result buffer (layout: final_layout())
   double* work;                // device scratch: 2 * pa * pa doubles
+  // When set, the eigen-decomposition is left to jacobi_grid_kernel: the matrix goes to
+  // defer_A (defer_m x defer_m, zero-padded to an even order) and *defer_ctl = 1 when the
+  // eigenpairs are wanted and defined (0 otherwise).
+  double* defer_A;
+  int32_t* defer_ctl;
+  int32_t defer_m;
 };
 // Offsets (in doubles) of the finalize result buffer.
 struct FinalLayout {
@@ -277,10 +283,35 @@ __host__ __device__ inline FinalLayout final_layout(int p, int pa) {
   return L;
 }
 // flags: [0] an exact integer entry did not fit 128 bits, [1] zero-variance columns,
-//        [2] Jacobi sweeps, [3] eigenpairs computed (1) or not (0)
+//        [2] Jacobi sweeps, [3] eigenpairs computed (1) or not (0),
+//        [5] a grid-wide wait of jacobi_grid_kernel ran out (1), [6] its seed basis was used (1)
 cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream);
 // d_params: count FinalParams in device memory, one block each
 cudaError_t launch_finalize_batched(const FinalParams* d_params, int count, cudaStream_t stream);
+
+// Cyclic Jacobi (the same round-robin ordering and rotations as the one-block solver)
+// spread over a cooperative grid: each round's 2 x 2 block updates of A and column-pair
+// updates of V are shared by all blocks, one grid-wide barrier per round.  A is double
+// buffered (a round reads a and writes b), so the rotation angles every block derives
+// from a are never overwritten under it.
+struct JacobiParams {
+  double* a;                // m x m, holds the matrix on entry (written by the finalize kernel)
+  double* b;                // m x m
+  double* v;                // m x m eigenvector accumulator
+  double* w;                // m x m, warm start product
+  const double* basis;      // pa x pa, row k = a previous eigenvector k, or nullptr (cold start)
+  double* slots;            // >= grid partial sums
+  unsigned int* bar;        // [0] arrivals, [1] generation, [2] error; zero before each launch
+  const int32_t* ctl;       // written by the finalize kernel: 1 = decompose
+  double* out;              // finalize result buffer
+  int64_t evals_off, evecs_off, flags_off;
+  int32_t pa, m;            // analysis columns; m = pa rounded up to even
+};
+// Doubles of scratch jacobi_grid_kernel needs for pa analysis columns (the five arrays above).
+size_t jacobi_scratch_doubles(int pa);
+// Blocks of the cooperative grid for pa columns on a device of `sms` SMs (0: not possible).
+int jacobi_grid_blocks(int pa, int sms);
+cudaError_t launch_jacobi_grid(const JacobiParams& J, int grid, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Table 1 generator and misc.

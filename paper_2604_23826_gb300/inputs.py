@@ -85,3 +85,23 @@ def gen_wide(torch, n: int, L, mu, seed: int, device, chunk: int = 1 << 22, out=
         x[:, r0:r1].copy_(y.t())
         del z, y
     return x
+
+
+def gen_correlated_host(n: int, L, mu, seed: int, row0: int = 0, block: int = 1 << 16):
+    """[p, n] float64 on the host: rows row0 .. row0 + n - 1 of X = Z L^T + mu, Z ~ N(0, 1).
+
+    Row block b (rows b*block .. (b+1)*block - 1 of the whole table) draws its Z from numpy's
+    generator seeded (seed, b), so any row range is reproducible without drawing the rows
+    before it, and chunks of a stream equal the same rows of one long table."""
+    L = np.asarray(L, dtype=np.float64)
+    p = L.shape[0]
+    out = np.empty((p, n), dtype=np.float64)
+    r = row0
+    while r < row0 + n:
+        b = r // block
+        z = np.random.default_rng([seed, b]).standard_normal((block, p))
+        lo = r - b * block
+        hi = min(block, row0 + n - b * block)
+        out[:, r - row0:r - row0 + hi - lo] = (z[lo:hi] @ L.T + mu).T
+        r = b * block + hi
+    return out
