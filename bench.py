@@ -618,15 +618,26 @@ def run_wide(args, rank: int, world: int, local_rank: int):
                 G.stats_accumulate(ctx, cm, nm, stream)
                 e1.record(stream)
                 ev.append((e0, e1))
-            an = G.stats_finalize(ctx)
             torch.cuda.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+            # the analysis (mean, cov, corr, PCA) of the accumulated statistics, then a streaming
+            # snapshot after 1 % more rows, its eigen-solve seeded by the first one's eigenvectors
+            t0 = time.perf_counter()
+            an = G.stats_finalize_warm(ctx, 0)
+            fin_ms = (time.perf_counter() - t0) * 1e3
+            G.stats_accumulate(ctx, [c[:nm // 100] for c in cm], nm // 100, stream)
+            G.stats_sync(ctx)
+            t0 = time.perf_counter()
+            an2 = G.stats_finalize_warm(ctx, 0, an.evecs)
+            snap_ms = (time.perf_counter() - t0) * 1e3
         top = np.asarray(an.evals[:10])
         results[mname] = {"rows": nm, "ms": ms, "rows_per_s": nm / (ms / 1e3),
                           "GB_per_s": 4 * p * nm / (ms / 1e3) / 1e9,
                           "hbm_frac": 4 * p * nm / (ms / 1e3) / 1e9 / peak,
                           "top10_eval_rel_to_1_over_k": float(np.max(np.abs(top - 1.0 / np.arange(1, 11)) *
                                                                      np.arange(1, 11))),
+                          "finalize_ms": fin_ms, "finalize_sweeps": an.sweeps,
+                          "snapshot_seeded_ms": snap_ms, "snapshot_seeded_sweeps": an2.sweeps,
                           "cov": an.cov}
     clocks = sampler.stop()
     ref = results.get("FP64S")
