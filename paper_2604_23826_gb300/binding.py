@@ -103,10 +103,16 @@ def load() -> ctypes.CDLL:
     L.stats_file_read_rows.argtypes = [cp, i64, i64, ctypes.POINTER(vp)]
     L.stats_file_check_table1.argtypes = [cp, ctypes.c_uint64, ctypes.c_uint64, i32, i64, ctypes.POINTER(i64)]
     L.stats_accumulate_file.argtypes = [vp, cp, i64, i64, i64, vp]
+    L.stats_csv_write.argtypes = [cp, i32, ctypes.POINTER(i32), i64, ctypes.POINTER(vp), cp]
+    L.stats_csv_write_table1.argtypes = [cp, ctypes.c_uint64, ctypes.c_uint64, i64, i32, i64]
+    L.stats_csv_parse.argtypes = [vp, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(vp), i64,
+                                  ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
+    L.stats_accumulate_csv.argtypes = [vp, cp, i64, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     for name in ("stats_init", "stats_accumulate", "stats_accumulate_host", "stats_merge", "stats_sync",
                  "stats_reset", "stats_raw", "stats_finalize", "stats_finalize_warm", "stats_export", "stats_import", "stats_set_grid",
                  "stats_table1_config", "stats_gen_table1", "stats_file_write", "stats_file_write_table1",
-                 "stats_file_info", "stats_file_read_rows", "stats_file_check_table1", "stats_accumulate_file"):
+                 "stats_file_info", "stats_file_read_rows", "stats_file_check_table1", "stats_accumulate_file",
+                 "stats_csv_write", "stats_csv_write_table1", "stats_csv_parse", "stats_accumulate_csv"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -574,3 +580,56 @@ def stats_accumulate_file(ctx: Ctx, path, row0: int = 0, nrows: int = -1, chunk_
     """Add file rows [row0, row0 + nrows) (nrows < 0: to the end) to ctx through pinned chunks."""
     _check(load().stats_accumulate_file(ctx.handle, _path(path), row0, nrows, chunk_rows, _stream_handle(stream)),
            "stats_accumulate_file")
+
+
+# ----------------------------------------------------------------------------- CSV text (stats_csv.h)
+T1_CSV_HEADER = "A,B,C,D,E,F,G,H,cotC,I,J,K"
+
+
+def _csv_error(code, where, bad):
+    err = StatsError(code, where)
+    err.bad_line = bad
+    return err
+
+
+def stats_csv_write(path, dtypes: Sequence[int], nrows: int, hcols: Sequence, header: str | None = None):
+    """Write an n x p table from host columns as CSV text (optional header line)."""
+    p = len(dtypes)
+    dt = (ctypes.c_int32 * p)(*dtypes)
+    _check(load().stats_csv_write(_path(path), p, dt, nrows, _ptr_array(hcols),
+                                  None if header is None else header.encode()), "stats_csv_write")
+
+
+def stats_csv_write_table1(path, seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0,
+                           chunk_rows: int = 0):
+    """Write Table 1 rows [row0, row0 + nrows), generated on the current device, as CSV with a header."""
+    _check(load().stats_csv_write_table1(_path(path), seed, row0, nrows, layout, chunk_rows),
+           "stats_csv_write_table1")
+
+
+def stats_csv_parse(d_text, nbytes: int, dtypes: Sequence[int], d_cols: Sequence, max_rows: int, stream=None) -> int:
+    """Parse the first len(dtypes) fields of every line of device text into device columns; returns
+    the number of lines, raises StatsError with .bad_line on a parse error."""
+    k = len(dtypes)
+    dt = (ctypes.c_int32 * k)(*dtypes)
+    n = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    code = load().stats_csv_parse(_ptr(d_text) if nbytes else None, nbytes, k, dt, _ptr_array(d_cols), max_rows,
+                                  ctypes.byref(n), ctypes.byref(bad), _stream_handle(stream))
+    if code != STATS_OK:
+        raise _csv_error(code, "stats_csv_parse", bad.value)
+    return n.value
+
+
+def stats_accumulate_csv(ctx: Ctx, path, skip_lines: int = 1, chunk_bytes: int = 0, stream=None) -> int:
+    """Stream a CSV file's first ctx.p fields into ctx (after skip_lines header lines); returns the
+    records added, raises StatsError with .bad_line (the file line) on a parse error."""
+    n = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    code = load().stats_accumulate_csv(ctx.handle, _path(path), skip_lines, chunk_bytes, ctypes.byref(n),
+                                       ctypes.byref(bad), _stream_handle(stream))
+    if code != STATS_OK:
+        err = _csv_error(code, "stats_accumulate_csv", bad.value)
+        err.rows_added = n.value
+        raise err
+    return n.value

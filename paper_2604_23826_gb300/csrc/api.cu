@@ -6,14 +6,19 @@
 #include <math.h>
 #include <string.h>
 
+#include <fcntl.h>
+#include <sys/stat.h>
+
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <unistd.h>
 
 #include "../../include/stats.h"
+#include "../../include/stats_csv.h"
 #include "../../include/stats_file.h"
 #include <cuda.h>
 
@@ -1152,6 +1157,185 @@ stats_status stats_accumulate_file(stats_ctx* ctx, const char* path, int64_t row
     s = enqueue_chunk(ctx, b, hc.data(), rows, st);
     if (s != STATS_OK) return s;
   }
+  return STATS_OK;
+}
+
+stats_status stats_accumulate_csv(stats_ctx* ctx, const char* path, int64_t skip_lines, int64_t chunk_bytes,
+                                  int64_t* nrows, int64_t* bad_line, void* stream) {
+  if (nrows) *nrows = 0;
+  if (bad_line) *bad_line = -1;
+  stats_status s = check_sticky(ctx);
+  if (s != STATS_OK) return s;
+  if (!path || skip_lines < 0 || chunk_bytes < 0) return STATS_EINVAL;
+  if (chunk_bytes == 0) chunk_bytes = int64_t(64) << 20;
+  chunk_bytes = std::max<int64_t>(chunk_bytes, 64);
+  const int fd = open(path, O_RDONLY);
+  if (fd < 0) return STATS_EIO;
+  struct Closer {
+    int fd;
+    ~Closer() { close(fd); }
+  } closer{fd};
+  struct stat sb;
+  if (fstat(fd, &sb) != 0) return STATS_EIO;
+  const int64_t fsize = sb.st_size;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int k = ctx->p;
+  // a record of k fields takes at least 2k bytes with its newline: the rows one chunk can hold
+  const int64_t row_cap = chunk_bytes / (2 * k) + 1;
+  s = ensure_staging(ctx, row_cap);
+  if (s != STATS_OK) return s;
+  // device: two text buffers, the parse scratch (every line of a chunk indexable), two column-pointer arrays
+  const int64_t ends_cap = chunk_bytes / 2 + 2;
+  const size_t text_bytes = (static_cast<size_t>(chunk_bytes) + 1 + 255) / 256 * 256;
+  const size_t scr = csv_scratch_bytes(chunk_bytes + 1, ends_cap, k);
+  char* dev = nullptr;
+  char* host = nullptr;
+  struct Frees {
+    char** d;
+    char** h;
+    ~Frees() {
+      if (*d) cudaFree(*d);
+      if (*h) cudaFreeHost(*h);
+    }
+  } frees{&dev, &host};
+  cudaError_t e = cudaMalloc(&dev, 2 * text_bytes + scr + 2 * 256 * sizeof(void*));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return STATS_ENOMEM;
+  }
+  CK(ctx, e);
+  e = cudaHostAlloc(&host, 2 * text_bytes + 256, cudaHostAllocDefault);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return STATS_ENOMEM;
+  }
+  CK(ctx, e);
+  char* d_text[2] = {dev, dev + text_bytes};
+  char* h_text[2] = {host, host + text_bytes};
+  struct Out {
+    int64_t total;
+    uint32_t status;
+    uint32_t pad;
+    unsigned long long bad;
+  }* out = reinterpret_cast<Out*>(host + 2 * text_bytes);
+  CsvScratch S;
+  csv_scratch_carve(dev + 2 * text_bytes, chunk_bytes + 1, ends_cap, k, S);
+  void** d_cols[2] = {reinterpret_cast<void**>(dev + 2 * text_bytes + scr),
+                      reinterpret_cast<void**>(dev + 2 * text_bytes + scr) + 256};
+  std::vector<void*> hc(2 * k);
+  for (int b = 0; b < 2; ++b)
+    for (int j = 0; j < k; ++j) hc[b * k + j] = static_cast<char*>(ctx->d_stage[b]) + ctx->stage_off[j];
+  CK(ctx, cudaMemcpy(d_cols[0], hc.data(), sizeof(void*) * k, cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy(d_cols[1], hc.data() + k, sizeof(void*) * k, cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy(S.dts, ctx->dtypes.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice));
+
+  // parallel read of [off, off + len) into buf
+  auto read_span = [&](char* buf, int64_t len, int64_t off) -> bool {
+    const int64_t piece = int64_t(8) << 20;
+    const int nt = static_cast<int>(std::min<int64_t>(16, (len + piece - 1) / piece));
+    if (nt <= 1) {
+      int64_t done = 0;
+      while (done < len) {
+        const ssize_t r = pread(fd, buf + done, static_cast<size_t>(len - done), off + done);
+        if (r <= 0) return false;
+        done += r;
+      }
+      return true;
+    }
+    std::vector<char> ok(nt, 1);
+    std::vector<std::thread> th;
+    const int64_t per = (len + nt - 1) / nt;
+    for (int i = 0; i < nt; ++i)
+      th.emplace_back([&, i] {
+        const int64_t a = std::min(len, i * per), z = std::min(len, a + per);
+        int64_t done = a;
+        while (done < z) {
+          const ssize_t r = pread(fd, buf + done, static_cast<size_t>(z - done), off + done);
+          if (r <= 0) {
+            ok[i] = 0;
+            return;
+          }
+          done += r;
+        }
+      });
+    for (auto& x : th) x.join();
+    for (int i = 0; i < nt; ++i)
+      if (!ok[i]) return false;
+    return true;
+  };
+
+  int64_t foff = 0;          // next file byte to read
+  int64_t carry = 0;         // bytes of a cut line, at carry_ptr in the previous buffer
+  const char* carry_ptr = nullptr;
+  int64_t lines_before = 0;  // file lines before the current chunk's first parsed line
+  int64_t skip = skip_lines;
+  int64_t added = 0;
+  std::vector<const void*> dc(k);
+  for (int64_t chunk = 0; foff < fsize || carry > 0; ++chunk) {
+    const int b = static_cast<int>(chunk & 1);
+    // the copy that last read h_text[b] has run (its parse was waited for)
+    CK(ctx, cudaEventSynchronize(ctx->ev_copied[b]));
+    char* buf = h_text[b];
+    if (carry > 0) memcpy(buf, carry_ptr, static_cast<size_t>(carry));
+    int64_t len = carry;
+    const int64_t want = std::min(chunk_bytes - len, fsize - foff);
+    if (want > 0) {
+      if (!read_span(buf + len, want, foff)) return STATS_EIO;
+      foff += want;
+      len += want;
+    }
+    int64_t whole;
+    if (foff >= fsize) {  // the end of the file closes the last line
+      if (len > 0 && buf[len - 1] != '\n') buf[len++] = '\n';
+      whole = len;
+      carry = 0;
+    } else {
+      whole = len;
+      while (whole > 0 && buf[whole - 1] != '\n') --whole;
+      if (whole == 0) {  // a line longer than a chunk
+        if (bad_line) *bad_line = lines_before;
+        return STATS_EFORMAT;
+      }
+      carry = len - whole;
+      carry_ptr = buf + whole;
+    }
+    int64_t start = 0;
+    while (skip > 0 && start < whole) {  // header lines
+      const char* nl = static_cast<const char*>(memchr(buf + start, '\n', static_cast<size_t>(whole - start)));
+      start = nl - buf + 1;
+      --skip;
+      ++lines_before;
+    }
+    if (start >= whole) continue;
+    const int64_t nb = whole - start;
+    CK(ctx, cudaMemcpyAsync(d_text[b], buf + start, static_cast<size_t>(nb), cudaMemcpyHostToDevice,
+                            ctx->copy_stream));
+    CK(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    CK(ctx, cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+    CK(ctx, cudaStreamWaitEvent(st, ctx->ev_done[b], 0));  // the pass that last read staging buffer b
+    S.cols = d_cols[b];
+    CK(ctx, cudaMemsetAsync(S.status, 0, sizeof(uint32_t), st));
+    CK(ctx, cudaMemsetAsync(S.bad, 0xFF, sizeof(unsigned long long), st));
+    CK(ctx, launch_csv_lines(d_text[b], nb, S, st));
+    CK(ctx, launch_csv_parse(d_text[b], S, k, row_cap, ctx->sms, st));
+    CK(ctx, cudaMemcpyAsync(&out->total, S.total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(&out->status, S.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaMemcpyAsync(&out->bad, S.bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(ctx, cudaStreamSynchronize(st));
+    if (out->status) {
+      if (bad_line) *bad_line = lines_before + static_cast<int64_t>(out->bad);
+      if (nrows) *nrows = added;
+      return (out->status & kCsvFormat) ? STATS_EFORMAT : STATS_ERANGE;
+    }
+    if (out->total > row_cap) return STATS_EFORMAT;  // unreachable: some line would be too short
+    for (int j = 0; j < k; ++j) dc[j] = hc[b * k + j];
+    s = launch_pass(ctx, dc.data(), out->total, st);
+    if (s != STATS_OK) return s;
+    CK(ctx, cudaEventRecord(ctx->ev_done[b], st));
+    lines_before += out->total;
+    added += out->total;
+  }
+  if (nrows) *nrows = added;
   return STATS_OK;
 }
 

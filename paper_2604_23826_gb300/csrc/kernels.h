@@ -314,6 +314,34 @@ int jacobi_grid_blocks(int pa, int sms);
 cudaError_t launch_jacobi_grid(const JacobiParams& J, int grid, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
+// CSV text on the device (csv.cu): line index and field parse.
+// ---------------------------------------------------------------------------
+constexpr int kCsvTile = 4096;  // bytes per line-counting tile
+// error bits of CsvScratch::status
+constexpr uint32_t kCsvFormat = 1u, kCsvRange = 2u;
+struct CsvScratch {
+  uint32_t* counts;          // newlines per tile
+  int64_t* offs;             // exclusive prefix of counts
+  int64_t* ends;             // ends[i]: offset of line i's '\n' (or the text's end), i < ends_cap
+  int64_t ends_cap;
+  int64_t* total;            // number of lines
+  uint32_t* status;          // kCsvFormat | kCsvRange
+  unsigned long long* bad;   // first offending line (all ones: none)
+  void** cols;               // k device column pointers
+  int32_t* dts;              // k stats_dtype values
+};
+// Bytes of scratch for texts of up to nbytes bytes, ends_cap lines and k fields; carve
+// lays the arrays out in base (256-byte aligned pieces).
+size_t csv_scratch_bytes(int64_t nbytes, int64_t ends_cap, int k);
+void csv_scratch_carve(void* base, int64_t nbytes, int64_t ends_cap, int k, CsvScratch& s);
+// Counts the lines of d_text[0, nbytes) and writes their ends (no host synchronisation).
+cudaError_t launch_csv_lines(const char* d_text, int64_t nbytes, const CsvScratch& s, cudaStream_t st);
+// Parses the first k fields of lines [0, min(*total, ends_cap)) into s.cols (rows below
+// row_cap are stored; every line is checked); status and bad must be reset before.
+cudaError_t launch_csv_parse(const char* d_text, const CsvScratch& s, int k, int64_t row_cap, int sms,
+                             cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // Table 1 generator and misc.
 // ---------------------------------------------------------------------------
 cudaError_t t1_upload_lut();  // builds the lookup tables with libm on the host, once per device
