@@ -64,7 +64,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
-    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10", "table1_file"),
+    ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10", "table1_file",
+                                                "table1_csv"),
                     default="table1",
                     help="table1: the headline line; tables4096 / wide256 / f32table: the FP32 workloads")
     ap.add_argument("--p", type=int, default=64, help="f32table: columns")
@@ -866,6 +867,112 @@ def run_table1_file(args, rank: int, world: int, local_rank: int):
         print(json.dumps(out), flush=True)
 
 
+def run_table1_csv(args, rank: int, world: int, local_rank: int):
+    """Table 1 as CSV text, the paper's starting representation: written once from the generator
+    (untimed); then (a) the text already in device memory parsed on the GPU into the twelve
+    columns, against the exact binary pass over the same rows, and (b) the file streamed into
+    the exact pass (pread into pinned chunks, H2D, GPU parse, pass; pages cached by the write)."""
+    import tempfile
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2604_23826_gb300 as G
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    seed = 1
+    layout = G.STATS_T1_L32 if args.layout == "L32" else G.STATS_T1_L16
+    bpr = BYTES_PER_ROW[layout]
+    n = int(args.n) if args.n != 1e9 else 50_000_000
+    row0 = rank * n
+    bind_host_to_gpu(local_rank)
+    tmp = tempfile.mkdtemp(prefix="sscsv_")
+    path = os.path.join(tmp, f"table1_{rank}.csv")
+    cfg = G.stats_table1_config(layout, row0 + n, G.STATS_EXACT)
+    tdt = {G.STATS_I16: torch.int16, G.STATS_I32: torch.int32, G.STATS_I64: torch.int64, G.STATS_F64: torch.float64}
+
+    def timed(fn, reps):
+        out = []
+        for i in range(args.warmup + reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                out.append(e0.elapsed_time(e1))
+        return sum(out) / len(out), r
+
+    try:
+        t0 = time.time()
+        G.stats_csv_write_table1(path, seed, n, layout, row0=row0)
+        write_s = time.time() - t0
+        text_bytes = os.path.getsize(path)
+        # (a) device-resident text: a prefix of whole lines of at most 4 GB
+        with open(path, "rb") as f:
+            f.readline()
+            blob = f.read(min(text_bytes, 4 << 30))
+        blob = blob[:blob.rfind(b"\n") + 1]
+        m = blob.count(b"\n")
+        d_text = torch.frombuffer(bytearray(blob), dtype=torch.uint8).to("cuda")
+        del blob
+        cols = [torch.empty(m, dtype=tdt[d], device="cuda") for d in cfg.dtypes]
+        parse_ms, got = timed(lambda: G.stats_csv_parse(d_text, d_text.numel(), cfg.dtypes, cols, m, stream), args.steps)
+        assert got == m
+        with G.stats_init(cfg) as ctx:
+            def bin_pass():
+                G.stats_reset(ctx)
+                G.stats_accumulate(ctx, cols, m, stream)
+            bin_ms, _ = timed(bin_pass, args.steps)
+            raw_dev = G.stats_raw(ctx)
+        del d_text, cols
+        torch.cuda.empty_cache()
+        # (b) the file streamed into the exact pass
+        with G.stats_init(cfg) as ctx:
+            def file_pass():
+                G.stats_reset(ctx)
+                r = G.stats_accumulate_csv(ctx, path, skip_lines=1, stream=stream)
+                G.stats_sync(ctx)
+                return r
+            file_ms, got = timed(file_pass, args.steps)
+            raw = G.stats_raw(ctx)
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
+        os.rmdir(tmp)
+    lo, hi = row0, row0 + n
+    checks = {"rows": got == n, "sumA": raw.s_exact[0] == hi * (hi + 1) // 2 - lo * (lo + 1) // 2,
+              "sumA2": raw.S_exact[0][0] == (hi * (hi + 1) * (2 * hi + 1) - lo * (lo + 1) * (2 * lo + 1)) // 6,
+              "prefix_sumA": raw_dev.s_exact[0] == (lo + m) * (lo + m + 1) // 2 - lo * (lo + 1) // 2}
+    text_per_row = text_bytes / n
+    config = {"workload": f"table1_csv_n{n:.0e}_seed{seed}_{args.layout}".replace("+", ""), "rows_per_gpu": n,
+              "p": 12, "layout": args.layout, "mode": "STATS_EXACT", "csv_bytes": text_bytes,
+              "csv_bytes_per_row": text_per_row, "binary_bytes_per_row": bpr,
+              "step": "stats_accumulate_csv (pread into pinned 64 MB chunks, H2D, GPU parse, exact pass) + sync",
+              "file": "CSV on the box's local disk, pages cached after the write",
+              "parallelism": f"rows sharded, {world} replica(s)"}
+    extra = {"checks": checks, "write_s": write_s,
+             "device_parse": {"rows": m, "ms": parse_ms,
+                              "rows_per_s": m / (parse_ms / 1e3), "text_GBps": m * text_per_row / (parse_ms / 1e3) / 1e9},
+             "binary_pass_same_rows": {"ms": bin_ms, "rows_per_s": m / (bin_ms / 1e3),
+                                       "GBps": m * bpr / (bin_ms / 1e3) / 1e9},
+             "parse_over_binary_pass": parse_ms / bin_ms,
+             "file_stream": {"ms": file_ms, "rows_per_s": n / (file_ms / 1e3),
+                             "text_GBps": text_bytes / (file_ms / 1e3) / 1e9}}
+    out = _base_line(args, world, METRIC, world * n / (file_ms / 1e3), file_ms, config,
+                     {"bound": "host file read", "achieved": text_bytes / (file_ms / 1e3) / 1e9, "peak": None,
+                      "unit": "GB/s", "frac": None, "traffic": None, "kernel": "csv_parse_kernel",
+                      "algorithmic_bytes": text_bytes},
+                     {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (file pass)"]},
+                     None, extra)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -890,6 +997,8 @@ def main():
             run_table1_stream(args, rank, world, local_rank)
         elif args.workload == "table1_file":
             run_table1_file(args, rank, world, local_rank)
+        elif args.workload == "table1_csv":
+            run_table1_csv(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -53,9 +53,11 @@ typedef enum {
   STATS_EOVERFLOW = 4,  /* an exact result does not fit its output type            */
   STATS_ETIMEOUT = 5,   /* a bounded device-side wait expired                      */
   STATS_ESTATE = 6,     /* ctx is sticky-failed, or the call is out of order       */
-  STATS_ERANGE = 7,     /* a value lay outside the digit field of its declared range */
+  STATS_ERANGE = 7,     /* a value lay outside the digit field of its declared range,
+                           or (stats_csv.h) outside its column type                  */
   STATS_EIO = 8,        /* a file could not be opened, read or written (stats_file.h) */
-  STATS_EFORMAT = 9,    /* a file is not a valid table file (stats_file.h)         */
+  STATS_EFORMAT = 9,    /* a file is not a valid table file (stats_file.h), or CSV
+                           text is malformed (stats_csv.h)                           */
   STATS_EMISMATCH = 10  /* a sampled file row differs from its source (stats_file.h) */
 } stats_status;
 

@@ -17,8 +17,8 @@
  *   - real fields: an optional sign, digits with an optional '.', optionally 'e' or 'E'
  *     and a signed decimal exponent (at most 4 digits); at least one mantissa digit.
  *     At most 19 significant digits (further digits must be zeros), and the value
- *     M * 10^E (M the integer of the significant digits) must have -38 <= E <= 19 and
- *     lie in the normal range of the column type, or be zero.  The writer prints FP64
+ *     must be M * 10^E for some integer M < 10^19 and -38 <= E <= 19 (magnitudes from
+ *     1e-38 to about 1e38) and lie in the normal range of the column type, or be zero.  The writer prints FP64
  *     values with 17 and FP32 values with 9 significant digits (round-trip exact).
  *   - Conversion is exact: the parser forms M * 10^E or M / 10^-E in integer
  *     arithmetic (up to 128-bit) and rounds once to nearest, ties to even, straight

@@ -1323,9 +1323,9 @@ stats_status stats_accumulate_csv(stats_ctx* ctx, const char* path, int64_t skip
     CK(ctx, cudaMemcpyAsync(&out->bad, S.bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(ctx, cudaStreamSynchronize(st));
     if (out->status) {
-      if (bad_line) *bad_line = lines_before + static_cast<int64_t>(out->bad);
+      if (bad_line) *bad_line = lines_before + static_cast<int64_t>(out->bad >> 2);
       if (nrows) *nrows = added;
-      return (out->status & kCsvFormat) ? STATS_EFORMAT : STATS_ERANGE;
+      return (out->bad & kCsvFormat) ? STATS_EFORMAT : STATS_ERANGE;
     }
     if (out->total > row_cap) return STATS_EFORMAT;  // unreachable: some line would be too short
     for (int j = 0; j < k; ++j) dc[j] = hc[b * k + j];
@@ -1799,9 +1799,9 @@ const char* stats_strerror(stats_status st) {
     case STATS_EOVERFLOW: return "exact result does not fit its output type";
     case STATS_ETIMEOUT: return "a bounded device-side wait expired";
     case STATS_ESTATE: return "context failed earlier or call out of order";
-    case STATS_ERANGE: return "a value lay outside the digit field of its declared range";
+    case STATS_ERANGE: return "a value lay outside its declared range or column type";
     case STATS_EIO: return "a file could not be opened, read or written";
-    case STATS_EFORMAT: return "not a valid table file (header, layout or size)";
+    case STATS_EFORMAT: return "malformed input (table file header, layout or size; or CSV text)";
     case STATS_EMISMATCH: return "a sampled file row differs from its source";
     default: return "unknown status";
   }

@@ -13,7 +13,7 @@
 //                      column j at the line's row (adjacent lines -> adjacent rows, so
 //                      the stores of a warp are contiguous).
 // Number conversion is exact.  A real field is M * 10^E with M < 10^19 (the significant
-// digits as an integer) and -38 <= E <= 19.  For E >= 0 the product M * 10^E is formed in
+// digits as an integer, trailing zeros moved into E) and -38 <= E <= 19.  For E >= 0 the product M * 10^E is formed in
 // 128-bit integers; for E < 0 the quotient M * 2^s / 10^-E is found by binary long
 // division (a 64-bit quotient and a sticky remainder bit).  Either way the exact value is
 // a 64-bit integer q plus a sticky fraction times a power of two, rounded once to
@@ -348,6 +348,15 @@ __device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, voi
   if (M == 0) {
     bits = neg ? (f64 ? (uint64_t(1) << 63) : (uint64_t(1) << 31)) : 0;
   } else {
+    // the same value with the exponent moved toward the supported range
+    while (E < 0 && M % 10u == 0) {
+      M /= 10u;
+      ++E;
+    }
+    while (E > 19 && M < 1000000000000000000ull) {
+      M *= 10u;
+      --E;
+    }
     if (E < -38 || E > 19) {
       status |= kCsvFormat;  // outside the supported exponent range
       return false;
@@ -396,9 +405,9 @@ __global__ void __launch_bounds__(256) csv_parse_kernel(const char* __restrict__
         p = f + 1;
       }
     }
-    if (status) {
+    if (status) {  // one error bit per line (its parse stops there); the smallest line wins
       atomicOr(S.status, status);
-      atomicMin(S.bad, static_cast<unsigned long long>(row));
+      atomicMin(S.bad, (static_cast<unsigned long long>(row) << 2) | status);
     }
   }
 }
@@ -683,8 +692,8 @@ stats_status stats_csv_parse(const char* d_text, int64_t nbytes, int32_t k, cons
   }
   if (res != STATS_OK) return res;
   if (out.status) {
-    if (bad_line) *bad_line = static_cast<int64_t>(out.bad);
-    return (out.status & kCsvFormat) ? STATS_EFORMAT : STATS_ERANGE;
+    if (bad_line) *bad_line = static_cast<int64_t>(out.bad >> 2);
+    return (out.bad & kCsvFormat) ? STATS_EFORMAT : STATS_ERANGE;
   }
   if (nrows) *nrows = out.total;
   return STATS_OK;

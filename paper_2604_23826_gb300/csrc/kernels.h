@@ -326,7 +326,7 @@ struct CsvScratch {
   int64_t ends_cap;
   int64_t* total;            // number of lines
   uint32_t* status;          // kCsvFormat | kCsvRange
-  unsigned long long* bad;   // first offending line (all ones: none)
+  unsigned long long* bad;   // (first offending line << 2) | its error bit (all ones: none)
   void** cols;               // k device column pointers
   int32_t* dts;              // k stats_dtype values
 };

@@ -116,7 +116,8 @@ def test_round_half_even_boundaries():
         if len(s) <= 19:
             cases.append(f"{s}e-{k}")
     cases += ["0", "-0", "0.0", "-0.000e5", "1", "-1", "1.5", "9999999999999999999", "0.1", "1e-37", "1e19",
-              "123456789012345678.9", "3402823466385288598e19", "2e-38", "2.000000000000000000e-38"]
+              "123456789012345678.9", "3402823466385288598e19", "2e-38",
+              "2.000000000000000000e-38", "1e20", "0.000500e-33"]
     text = "\n".join(f"{c},{c}" for c in cases) + "\n"
     n, (c64, c32) = _parse(text, [G.STATS_F64, G.STATS_F32])
     assert n == len(cases)
@@ -141,7 +142,7 @@ def test_integers_bounds_and_fields_past_k():
 @pytest.mark.parametrize("bad,code", [
     ("1,x", G.STATS_EFORMAT), ("1", G.STATS_EFORMAT), ("", G.STATS_EFORMAT), ("1,", G.STATS_EFORMAT),
     ("1.5,2", G.STATS_EFORMAT), ("32768,1", G.STATS_ERANGE), ("-32769,1", G.STATS_ERANGE),
-    ("1,1e-39", G.STATS_EFORMAT), ("1,1e20", G.STATS_EFORMAT), ("1,12345678901234567891", G.STATS_EFORMAT),
+    ("1,1e-39", G.STATS_EFORMAT), ("1,1e40", G.STATS_EFORMAT), ("1,12345678901234567891", G.STATS_EFORMAT),
     ("1,1e-38", G.STATS_ERANGE), ("1,1.2.3", G.STATS_EFORMAT), ("1,1e", G.STATS_EFORMAT),
     ("1,1e12345", G.STATS_EFORMAT), ("1,.", G.STATS_EFORMAT), ("1,--1", G.STATS_EFORMAT),
     ("12345678901234567890,1", G.STATS_EFORMAT)])
