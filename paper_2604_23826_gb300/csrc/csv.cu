@@ -145,6 +145,34 @@ __global__ void __launch_bounds__(kCsvThreads) csv_index_kernel(const char* __re
 }
 
 // ------------------------------- exact decimal -> binary -------------------------------
+constexpr int kCsvFastK = 27;  // 5^27 < 2^63: one-word divisors for 10^-k, k <= 27
+struct CsvTables {
+  uint64_t p10[20];
+  uint64_t dn[kCsvFastK + 1];
+  uint64_t v[kCsvFastK + 1];
+  int32_t z[kCsvFastK + 1];
+  int32_t pad;
+};
+static_assert(sizeof(CsvTables) % 8 == 0, "copied as 64-bit words");
+
+// Built on the host in exact integer arithmetic.
+CsvTables make_csv_tables() {
+  CsvTables T{};
+  uint64_t p = 1;
+  for (int i = 0; i < 20; ++i, p *= 10u) T.p10[i] = p;
+  uint64_t f = 1;
+  for (int k = 1; k <= kCsvFastK; ++k) {
+    f *= 5u;
+    const int z = __builtin_clzll(f);
+    const uint64_t dn = f << z;
+    const unsigned __int128 all = ~static_cast<unsigned __int128>(0);
+    T.dn[k] = dn;
+    T.z[k] = z;
+    T.v[k] = static_cast<uint64_t>(all / dn - (static_cast<unsigned __int128>(1) << 64));
+  }
+  return T;
+}
+
 struct U128 {
   uint64_t lo, hi;
 };
@@ -203,12 +231,12 @@ __device__ uint64_t round_assemble(uint64_t q, bool sticky, int e2, int t, bool 
   return bits | (neg ? (1u << 31) : 0u);
 }
 
-// M * 10^E correctly rounded to t bits (M > 0, -38 <= E <= 19), as IEEE bits
-__device__ uint64_t decimal_to_bits(uint64_t M, int E, int t, bool neg, uint32_t& status) {
+// M * 10^E correctly rounded to t bits (M > 0, -38 <= E <= 19), as IEEE bits.  T holds
+// 10^0 .. 10^19 and, for 1 <= k <= kCsvFastK, 5^k normalised (shifted left until its top
+// bit is set) with its reciprocal v = floor((2^128 - 1) / (5^k << z)) - 2^64.
+__device__ uint64_t decimal_to_bits(uint64_t M, int E, int t, bool neg, uint32_t& status, const CsvTables& T) {
   if (E >= 0) {
-    uint64_t p10 = 1;
-    for (int i = 0; i < E; ++i) p10 *= 10u;  // 10^19 < 2^64
-    const U128 P = mul64x64(M, p10);
+    const U128 P = mul64x64(M, T.p10[E]);  // 10^19 < 2^64, the product < 2^128
     const int bl = bitlen128(P);
     uint64_t q;
     bool sticky = false;
@@ -223,21 +251,40 @@ __device__ uint64_t decimal_to_bits(uint64_t M, int E, int t, bool neg, uint32_t
     }
     return round_assemble(q, sticky, e2, t, neg, status);
   }
-  U128 D{1, 0};
-  for (int i = 0; i < -E; ++i) D = mul128x10(D);  // 10^38 < 2^127
-  const int bM = bitlen64(M), bD = bitlen128(D);
-  const int s = 63 + bD - bM;  // M 2^s / D lies in [2^62, 2^64)
-  U128 R;
-  uint64_t q = 0;
-  int steps;
-  if (bM < bD) {
-    R = shl128(U128{M, 0}, bD - 1 - bM);  // < D: the leading quotient bits are zero
-    steps = s - (bD - 1 - bM);
-  } else {  // D < 2^64
-    q = M / D.lo;
-    R = U128{M % D.lo, 0};
-    steps = s;
+  const int k = -E, bM = bitlen64(M);
+  if (k <= kCsvFastK) {
+    // M / 10^k = (M 2^a / 5^k) 2^-(a + k) with a = 63 + bitlen(5^k) - bitlen(M), so that
+    // q = floor(M 2^a / 5^k) lies in [2^62, 2^64).  With 5^k normalised to dn = 5^k 2^z,
+    // q = floor(u / dn) for u = M 2^(a + z) = M 2^(127 - bitlen(M)) (a 128-bit numerator
+    // whose high word is below dn): one division by an invariant word with its
+    // precomputed reciprocal (Moller and Granlund 2011) and the exact remainder.
+    const uint64_t dn = T.dn[k], v = T.v[k];
+    const int bD = 64 - T.z[k];
+    const int sh = 127 - bM;  // 63 .. 126
+    const uint64_t u1 = sh >= 64 ? M << (sh - 64) : M >> 1;
+    const uint64_t u0 = sh >= 64 ? 0 : M << 63;
+    const U128 qq = mul64x64(v, u1);
+    const uint64_t q0 = qq.lo + u0;
+    uint64_t q1 = qq.hi + u1 + (q0 < qq.lo ? 1u : 0u) + 1u;
+    uint64_t r = u0 - q1 * dn;
+    if (r > q0) {
+      q1 -= 1u;
+      r += dn;
+    }
+    if (r >= dn) {
+      q1 += 1u;
+      r -= dn;
+    }
+    return round_assemble(q1, r != 0, -(63 + bD - bM + k), t, neg, status);
   }
+  // 10^k above 2^64: binary long division, one quotient bit per step
+  U128 D{1, 0};
+  for (int i = 0; i < k; ++i) D = mul128x10(D);  // 10^38 < 2^127
+  const int bD = bitlen128(D);
+  const int s = 63 + bD - bM;  // M 2^s / D lies in [2^62, 2^64)
+  U128 R = shl128(U128{M, 0}, bD - 1 - bM);  // M < 2^64 < D here: the leading quotient bits are zero
+  const int steps = s - (bD - 1 - bM);
+  uint64_t q = 0;
   for (int i = 0; i < steps; ++i) {
     R = shl128(R, 1);
     q <<= 1;
@@ -251,36 +298,37 @@ __device__ uint64_t decimal_to_bits(uint64_t M, int E, int t, bool neg, uint32_t
 
 __device__ __forceinline__ bool is_digit(char c) { return c >= '0' && c <= '9'; }
 
-// Parse one field [p, e) as column type dt and store it at dst.  Returns false (status
-// set) on an error.
-__device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, void* dst, uint32_t& status) {
-  if (p >= e) {
-    status |= kCsvFormat;
-    return false;
-  }
+// Parse the field that starts at p (ended by ',' or the line end e) as column type dt and
+// store it at dst.  Returns the terminator's position, or -1 (status set) on an error.
+__device__ int64_t parse_field(const char* t, int64_t p, int64_t e, int32_t dt, void* dst, uint32_t& status,
+                               const CsvTables& T) {
+  char c = p < e ? t[p] : ',';
   bool neg = false;
-  if (t[p] == '+' || t[p] == '-') {
-    neg = t[p] == '-';
+  if (c == '+' || c == '-') {
+    neg = c == '-';
     ++p;
+    c = p < e ? t[p] : ',';
   }
   if (dt == STATS_I16 || dt == STATS_I32 || dt == STATS_I64) {
-    if (p >= e || e - p > STATS_CSV_MAX_DIGITS) {
-      status |= kCsvFormat;
-      return false;
-    }
     uint64_t v = 0;
-    for (; p < e; ++p) {
-      const char c = t[p];
-      if (!is_digit(c)) {
+    int nd = 0;
+    while (c != ',') {
+      if (!is_digit(c) || ++nd > STATS_CSV_MAX_DIGITS) {
         status |= kCsvFormat;
-        return false;
+        return -1;
       }
       v = v * 10u + static_cast<uint64_t>(c - '0');
+      ++p;
+      c = p < e ? t[p] : ',';
+    }
+    if (nd == 0) {
+      status |= kCsvFormat;
+      return -1;
     }
     const uint64_t lim = dt == STATS_I16 ? 32767u : dt == STATS_I32 ? 2147483647u : 9223372036854775807ull;
     if (v > lim + (neg ? 1u : 0u)) {
       status |= kCsvRange;
-      return false;
+      return -1;
     }
     const int64_t x = neg ? static_cast<int64_t>(0 - v) : static_cast<int64_t>(v);
     if (dt == STATS_I16)
@@ -289,14 +337,13 @@ __device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, voi
       *static_cast<int32_t*>(dst) = static_cast<int32_t>(x);
     else
       *static_cast<int64_t*>(dst) = x;
-    return true;
+    return p;
   }
   // real: digits [. digits] [e|E [+-] digits]
   uint64_t M = 0;
-  int nsig = 0, E = 0, ndig = 0;
+  int nsig = 0, E = 0, ndig = 0, tz = 0;  // tz: trailing zero digits of M
   bool point = false;
-  for (; p < e; ++p) {
-    const char c = t[p];
+  for (;; ++p, c = p < e ? t[p] : ',') {
     if (c == '.') {
       if (point) break;
       point = true;
@@ -312,36 +359,39 @@ __device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, voi
     if (nsig < STATS_CSV_MAX_DIGITS) {
       M = M * 10u + static_cast<uint64_t>(d);
       ++nsig;
+      tz = d == 0 ? tz + 1 : 0;
       if (point) --E;
     } else if (d != 0) {
       status |= kCsvFormat;  // more significant digits than supported
-      return false;
+      return -1;
     } else if (!point) {
       ++E;  // a zero past the kept digits, before the point
     }
   }
   if (ndig == 0) {
     status |= kCsvFormat;
-    return false;
+    return -1;
   }
-  if (p < e && (t[p] == 'e' || t[p] == 'E')) {
+  if (c == 'e' || c == 'E') {
     ++p;
+    c = p < e ? t[p] : ',';
     bool eneg = false;
-    if (p < e && (t[p] == '+' || t[p] == '-')) {
-      eneg = t[p] == '-';
+    if (c == '+' || c == '-') {
+      eneg = c == '-';
       ++p;
+      c = p < e ? t[p] : ',';
     }
     int x = 0, nx = 0;
-    for (; p < e && is_digit(t[p]); ++p, ++nx) x = x * 10 + (t[p] - '0');
+    for (; is_digit(c); ++p, c = p < e ? t[p] : ',', ++nx) x = x * 10 + (c - '0');
     if (nx == 0 || nx > 4) {
       status |= kCsvFormat;
-      return false;
+      return -1;
     }
     E += eneg ? -x : x;
   }
-  if (p != e) {
+  if (c != ',') {
     status |= kCsvFormat;
-    return false;
+    return -1;
   }
   const bool f64 = dt == STATS_F64;
   uint64_t bits = 0;
@@ -349,9 +399,10 @@ __device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, voi
     bits = neg ? (f64 ? (uint64_t(1) << 63) : (uint64_t(1) << 31)) : 0;
   } else {
     // the same value with the exponent moved toward the supported range
-    while (E < 0 && M % 10u == 0) {
-      M /= 10u;
-      ++E;
+    if (E < 0 && tz > 0) {  // trailing zeros of M (counted while parsing: no 64-bit remainders)
+      const int n = min(tz, -E);
+      M /= T.p10[n];
+      E += n;
     }
     while (E > 19 && M < 1000000000000000000ull) {
       M *= 10u;
@@ -359,20 +410,20 @@ __device__ bool parse_field(const char* t, int64_t p, int64_t e, int32_t dt, voi
     }
     if (E < -38 || E > 19) {
       status |= kCsvFormat;  // outside the supported exponent range
-      return false;
+      return -1;
     }
     uint32_t st = 0;
-    bits = decimal_to_bits(M, E, f64 ? 53 : 24, neg, st);
+    bits = decimal_to_bits(M, E, f64 ? 53 : 24, neg, st, T);
     if (st) {
       status |= st;
-      return false;
+      return -1;
     }
   }
   if (f64)
     *static_cast<uint64_t*>(dst) = bits;
   else
     *static_cast<uint32_t*>(dst) = static_cast<uint32_t>(bits);
-  return true;
+  return p;
 }
 
 __device__ __forceinline__ int dtype_size(int32_t dt) {
@@ -380,7 +431,11 @@ __device__ __forceinline__ int dtype_size(int32_t dt) {
 }
 
 __global__ void __launch_bounds__(256) csv_parse_kernel(const char* __restrict__ t, CsvScratch S, int k,
-                                                       int64_t row_cap) {
+                                                       int64_t row_cap, const __grid_constant__ CsvTables TP) {
+  __shared__ CsvTables T;
+  for (int i = threadIdx.x; i < static_cast<int>(sizeof(CsvTables) / 8); i += blockDim.x)
+    reinterpret_cast<uint64_t*>(&T)[i] = reinterpret_cast<const uint64_t*>(&TP)[i];
+  __syncthreads();
   const int64_t nl = min(*S.total, S.ends_cap);
   for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < nl;
        row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -390,13 +445,12 @@ __global__ void __launch_bounds__(256) csv_parse_kernel(const char* __restrict__
     uint32_t status = 0;
     const bool store = row < row_cap;
     for (int j = 0; j < k; ++j) {
-      int64_t f = p;
-      while (f < e && t[f] != ',') ++f;
       const int32_t dt = S.dts[j];
       uint64_t scratch;
       void* dst = store ? static_cast<void*>(static_cast<char*>(S.cols[j]) + row * dtype_size(dt))
                         : static_cast<void*>(&scratch);
-      if (!parse_field(t, p, f, dt, dst, status)) break;
+      const int64_t f = parse_field(t, p, e, dt, dst, status, T);
+      if (f < 0) break;
       if (j + 1 < k) {
         if (f >= e) {  // fewer than k fields
           status |= kCsvFormat;
@@ -458,7 +512,8 @@ cudaError_t launch_csv_parse(const char* d_text, const CsvScratch& s, int k, int
                              cudaStream_t st) {
   const int64_t want = (s.ends_cap + 255) / 256;
   const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 8)));
-  csv_parse_kernel<<<grid, 256, 0, st>>>(d_text, s, k, row_cap);
+  static const CsvTables tables = make_csv_tables();
+  csv_parse_kernel<<<grid, 256, 0, st>>>(d_text, s, k, row_cap, tables);
   return cudaGetLastError();
 }
 
