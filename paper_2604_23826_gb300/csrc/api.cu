@@ -823,13 +823,14 @@ stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on, const double* 
   JacobiParams J{};
   if (grid > 0) {
     if (!c->d_jac) CK(c, cudaMalloc(&c->d_jac, jacobi_scratch_doubles(pa) * sizeof(double)));
-    const size_t m = pa + (pa & 1);
+    const size_t m = (pa + 15) / 16 * 16;
     J.a = c->d_jac;
     J.b = J.a + m * m;
     J.v = J.b + m * m;
     J.w = J.v + m * m;
     double* basis = J.w + m * m;
-    J.slots = basis + static_cast<size_t>(pa) * pa;
+    J.q = basis + static_cast<size_t>(pa) * pa;
+    J.slots = J.q + (m / 16) * 256;
     J.bar = reinterpret_cast<unsigned int*>(J.slots + 1024);
     J.ctl = reinterpret_cast<const int32_t*>(J.bar + 4);
     J.basis = seed ? basis : nullptr;

@@ -484,7 +484,9 @@ cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream) {
 namespace {
 
 constexpr int kJacThreads = 256;
-constexpr int kJacMaxItems = 4;                       // work items per thread and round
+constexpr int kJW = 8;         // indices per Jacobi block
+constexpr int kJP = 2 * kJW;   // order of a block pair's diagonal problem; kJP x kJP = kJacThreads
+static_assert(kJP * kJP == kJacThreads, "one thread per entry of a block-pair tile");
 constexpr unsigned long long kGridWaitNs = 2000000000ull;  // a grid-wide wait gives up after 2 s
 
 __device__ __forceinline__ void pair_of(int r, int i, int m, int& p, int& q) {
@@ -591,25 +593,24 @@ __device__ void grid_matmul(const double* X, const double* Y, double* Z, int m, 
 }  // namespace
 
 size_t jacobi_scratch_doubles(int pa) {
-  const size_t m = pa + (pa & 1);
-  return 4 * m * m + static_cast<size_t>(pa) * pa + 1024 + 8;
+  const size_t m = (pa + kJP - 1) / kJP * kJP;
+  return 4 * m * m + static_cast<size_t>(pa) * pa + (m / kJP) * kJP * kJP + 1024 + 8;
 }
 
 int jacobi_grid_blocks(int pa, int sms) {
-  const int m = pa + (pa & 1), h = m / 2;
-  const int items = h * h + pa * h;
-  int g = (items + kJacThreads - 1) / kJacThreads;
+  const int m = (pa + kJP - 1) / kJP * kJP, np = m / kJP;
+  int g = 2 * np * np;  // the work items of a block round's second step
   if (g > sms) g = sms;
   if (g > 512) g = 512;  // two partial sums per block fit the 1024-double slot area
-  if (g < 1) g = 1;
-  if (static_cast<int64_t>(g) * kJacThreads * kJacMaxItems < items) return 0;
-  return g;
+  return g < 1 ? 1 : g;
 }
 
 __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __grid_constant__ JacobiParams J) {
   __shared__ double s_c[128], s_s[128];
   __shared__ double s_red[kJacThreads / 32];
   __shared__ double s_x[16][17], s_y[16][17];
+  __shared__ double s_S[kJP][kJP + 1], s_Q[kJP][kJP + 1], s_X[kJP][kJP + 1], s_T[kJP][kJP + 1],
+      s_QA[kJP][kJP + 1], s_QB[kJP][kJP + 1];
   __shared__ double s_d[256];
   __shared__ int s_order[256];
   __shared__ double s_bv[kJacThreads / 32];
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
   __shared__ int s_ok;
   if (__ldcg(J.ctl) == 0) return;  // the finalize kernel found the eigenpairs undefined
   const int tid = threadIdx.x;
-  const int pa = J.pa, m = J.m, h = m / 2;
+  const int pa = J.pa, m = J.m;
   const int nthreads = gridDim.x * kJacThreads;
   const int gtid = blockIdx.x * kJacThreads + tid;
   unsigned int gen = 0;
@@ -703,8 +704,10 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
     __syncthreads();
     const double fro2 = s_val;
     __syncthreads();
-    const int nA = h * h, nItems = h * h + pa * h;
+    const int nb = m / kJW, np = nb / 2;  // index blocks of kJW, and the pairs of a block round
+    const int lr_ = tid / kJP, lc_ = tid % kJP;  // this thread's entry of a kJP x kJP tile
     int sweep = 0;
+    double prev_off = 0.0;
     for (; sweep < 60; ++sweep) {
       if (tid == 0) {
         double t = 0.0;
@@ -714,78 +717,110 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
       __syncthreads();
       const double off = s_val;
       __syncthreads();
-      if (off == 0.0 || off <= 1e-34 * fro2) break;
-      for (int round = 0; round < m - 1; ++round) {
-        // this thread's items: loads first, so their latency overlaps the angle computation
-        double x0[kJacMaxItems], x1[kJacMaxItems], x2[kJacMaxItems], x3[kJacMaxItems];
-#pragma unroll
-        for (int u = 0; u < kJacMaxItems; ++u) {
-          const int it = gtid + u * nthreads;
-          x0[u] = x1[u] = x2[u] = x3[u] = 0.0;
-          if (it < nA) {
-            int pi, qi, pj, qj;
-            pair_of(round, it / h, m, pi, qi);
-            pair_of(round, it % h, m, pj, qj);
-            x0[u] = __ldcg(A + static_cast<size_t>(pi) * m + pj);
-            x1[u] = __ldcg(A + static_cast<size_t>(pi) * m + qj);
-            x2[u] = __ldcg(A + static_cast<size_t>(qi) * m + pj);
-            x3[u] = __ldcg(A + static_cast<size_t>(qi) * m + qj);
-          } else if (it < nItems) {
-            const int k = (it - nA) / h;
-            int pj, qj;
-            pair_of(round, (it - nA) % h, m, pj, qj);
-            x0[u] = __ldcg(V + static_cast<size_t>(k) * m + pj);
-            x1[u] = __ldcg(V + static_cast<size_t>(k) * m + qj);
-          }
-        }
-        // rotation angles of this round, from A (every block derives all of them)
-        for (int i = tid; i < h; i += kJacThreads) {
-          int p, q;
-          pair_of(round, i, m, p, q);
-          double c = 1.0, s = 0.0;
-          if (q < pa) {
-            // three independent loads in flight at once
-            const double apq = __ldcg(A + static_cast<size_t>(p) * m + q);
-            const double app = __ldcg(A + static_cast<size_t>(p) * m + p);
-            const double aqq = __ldcg(A + static_cast<size_t>(q) * m + q);
-            if (apq != 0.0) {
-              const double theta = (aqq - app) / (2.0 * apq);
-              const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-              c = 1.0 / sqrt(t * t + 1.0);
-              s = t * c;
+      // converged: off-diagonal mass negligible, or (block updates leave rounding noise in every
+      // off-diagonal entry) no longer falling quadratically once below 1e-26 of ||A||^2
+      if (off == 0.0 || off <= 1e-34 * fro2 || (sweep > 0 && off <= 1e-26 * fro2 && off > 0.0625 * prev_off)) break;
+      prev_off = off;
+      for (int br = 0; br < nb - 1; ++br) {
+        // (1) every block pair's kJP x kJP diagonal problem: one cyclic Jacobi sweep in shared
+        //     memory, its rotations accumulated in Q (to J.q), its result written to B
+        for (int P = blockIdx.x; P < np; P += gridDim.x) {
+          int bi, bj;
+          pair_of(br, P, nb, bi, bj);
+          const int gr = lr_ < kJW ? bi * kJW + lr_ : bj * kJW + lr_ - kJW;
+          const int gc = lc_ < kJW ? bi * kJW + lc_ : bj * kJW + lc_ - kJW;
+          s_S[lr_][lc_] = __ldcg(A + static_cast<size_t>(gr) * m + gc);
+          s_Q[lr_][lc_] = lr_ == lc_ ? 1.0 : 0.0;
+          __syncthreads();
+          for (int lr = 0; lr < kJP - 1; ++lr) {
+            if (tid < kJP / 2) {
+              int p, q;
+              pair_of(lr, tid, kJP, p, q);
+              double c = 1.0, sn = 0.0;
+              const double apq = s_S[p][q];
+              if (apq != 0.0) {
+                // the one-block solver's t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), theta =
+                // d / (2 apq), d = aqq - app, multiplied through by 2 |apq|: one square root and
+                // one division in the dependent chain instead of two of each
+                const double d = s_S[q][q] - s_S[p][p];
+                const double t = (d >= 0.0 ? 2.0 * apq : -2.0 * apq) / (fabs(d) + sqrt(d * d + 4.0 * apq * apq));
+                c = rsqrt(t * t + 1.0);
+                sn = t * c;
+              }
+              s_c[tid] = c;
+              s_s[tid] = sn;
             }
+            __syncthreads();
+            if (tid < (kJP / 2) * kJP) {  // rows p, q
+              const int i = tid / kJP, k = tid % kJP;
+              int p, q;
+              pair_of(lr, i, kJP, p, q);
+              const double c = s_c[i], sn = s_s[i];
+              if (sn != 0.0) {
+                const double apk = s_S[p][k], aqk = s_S[q][k];
+                s_S[p][k] = c * apk - sn * aqk;
+                s_S[q][k] = sn * apk + c * aqk;
+              }
+            }
+            __syncthreads();
+            {  // columns p, q of S (first half of the threads) and of Q (second half)
+              const int u = tid % ((kJP / 2) * kJP);
+              const int i = u / kJP, k = u % kJP;
+              int p, q;
+              pair_of(lr, i, kJP, p, q);
+              const double c = s_c[i], sn = s_s[i];
+              const bool onS = tid < (kJP / 2) * kJP;
+              double(*X)[kJP + 1] = onS ? s_S : s_Q;
+              if (sn != 0.0) {
+                const double xkp = X[k][p], xkq = X[k][q];
+                // the rotated pair's off-diagonal entries are zero by construction
+                X[k][p] = (onS && k == q) ? 0.0 : c * xkp - sn * xkq;
+                X[k][q] = (onS && k == p) ? 0.0 : sn * xkp + c * xkq;
+              }
+            }
+            __syncthreads();
           }
-          s_c[i] = c;
-          s_s[i] = s;
+          __stcg(J.q + static_cast<size_t>(P) * kJP * kJP + tid, s_Q[lr_][lc_]);
+          __stcg(B + static_cast<size_t>(gr) * m + gc, s_S[lr_][lc_]);
+          __syncthreads();
         }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < kJacMaxItems; ++u) {
-          const int it = gtid + u * nthreads;
-          if (it < nA) {
-            const int i = it / h, j = it % h;
-            int pi, qi, pj, qj;
-            pair_of(round, i, m, pi, qi);
-            pair_of(round, j, m, pj, qj);
-            const double ci = s_c[i], si = s_s[i], cj = s_c[j], sj = s_s[j];
-            // rows (pi, qi), then columns (pj, qj)
-            const double r0 = ci * x0[u] - si * x2[u], r2 = si * x0[u] + ci * x2[u];
-            const double r1 = ci * x1[u] - si * x3[u], r3 = si * x1[u] + ci * x3[u];
-            double y0 = cj * r0 - sj * r1, y1 = sj * r0 + cj * r1;
-            double y2 = cj * r2 - sj * r3, y3 = sj * r2 + cj * r3;
-            if (i == j) y1 = y2 = 0.0;  // the rotated pair's off-diagonal entry is zero by construction
-            __stcg(B + static_cast<size_t>(pi) * m + pj, y0);
-            __stcg(B + static_cast<size_t>(pi) * m + qj, y1);
-            __stcg(B + static_cast<size_t>(qi) * m + pj, y2);
-            __stcg(B + static_cast<size_t>(qi) * m + qj, y3);
-          } else if (it < nItems) {
-            const int k = (it - nA) / h, j = (it - nA) % h;
-            int pj, qj;
-            pair_of(round, j, m, pj, qj);
-            const double cj = s_c[j], sj = s_s[j];
-            __stcg(V + static_cast<size_t>(k) * m + pj, cj * x0[u] - sj * x1[u]);
-            __stcg(V + static_cast<size_t>(k) * m + qj, sj * x0[u] + cj * x1[u]);
+        if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+        // (2) the other blocks of A, Q_P^T A[P rows][P' cols] Q_P' (into B), and V's columns,
+        //     V[rows][P' cols] Q_P' (in place: every entry belongs to one item)
+        const int nA = np * np, nItems = nA + (m / kJP) * np;
+        for (int it = blockIdx.x; it < nItems; it += gridDim.x) {
+          if (it < nA && it / np == it % np) continue;  // diagonal blocks came from step (1)
+          const bool isA = it < nA;
+          const int P2 = isA ? it % np : (it - nA) % np;
+          int ci, cj;
+          pair_of(br, P2, nb, ci, cj);
+          const int gc = lc_ < kJW ? ci * kJW + lc_ : cj * kJW + lc_ - kJW;
+          int gr;
+          if (isA) {
+            int bi, bj;
+            pair_of(br, it / np, nb, bi, bj);
+            gr = lr_ < kJW ? bi * kJW + lr_ : bj * kJW + lr_ - kJW;
+            s_X[lr_][lc_] = __ldcg(A + static_cast<size_t>(gr) * m + gc);
+            s_QA[lr_][lc_] = __ldcg(J.q + static_cast<size_t>(it / np) * kJP * kJP + tid);
+          } else {
+            gr = ((it - nA) / np) * kJP + lr_;
+            s_X[lr_][lc_] = __ldcg(V + static_cast<size_t>(gr) * m + gc);
           }
+          s_QB[lr_][lc_] = __ldcg(J.q + static_cast<size_t>(P2) * kJP * kJP + tid);
+          __syncthreads();
+          if (isA) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < kJP; ++k) t = fma(s_QA[k][lr_], s_X[k][lc_], t);
+            s_T[lr_][lc_] = t;
+            __syncthreads();
+          }
+          double (*L)[kJP + 1] = isA ? s_T : s_X;
+          double y = 0.0;
+#pragma unroll
+          for (int k = 0; k < kJP; ++k) y = fma(L[lr_][k], s_QB[k][lc_], y);
+          __stcg((isA ? B : V) + static_cast<size_t>(gr) * m + gc, y);
+          __syncthreads();
         }
         double* t = A;
         A = B;

@@ -289,23 +289,25 @@ cudaError_t launch_finalize(const FinalParams& P, cudaStream_t stream);
 // d_params: count FinalParams in device memory, one block each
 cudaError_t launch_finalize_batched(const FinalParams* d_params, int count, cudaStream_t stream);
 
-// Cyclic Jacobi (the same round-robin ordering and rotations as the one-block solver)
-// spread over a cooperative grid: each round's 2 x 2 block updates of A and column-pair
-// updates of V are shared by all blocks, one grid-wide barrier per round.  A is double
-// buffered (a round reads a and writes b), so the rotation angles every block derives
-// from a are never overwritten under it.
+// Block-cyclic Jacobi spread over a cooperative grid.  The indices are cut into blocks
+// of 8; in each block round (the round-robin ordering over blocks) every pair of blocks
+// solves its 16 x 16 diagonal problem with one cyclic Jacobi sweep (the one-block
+// solver's rotation formula) in shared memory, then all 16 x 16 blocks of A and V are
+// updated with the pairs' accumulated rotations: two grid-wide barriers per block round.
+// A is double buffered (a round reads a and writes b).
 struct JacobiParams {
   double* a;                // m x m, holds the matrix on entry (written by the finalize kernel)
   double* b;                // m x m
   double* v;                // m x m eigenvector accumulator
   double* w;                // m x m, warm start product
+  double* q;                // (m / 16) x 16 x 16: the rotation of every block pair of a round
   const double* basis;      // pa x pa, row k = a previous eigenvector k, or nullptr (cold start)
   double* slots;            // >= grid partial sums
   unsigned int* bar;        // [0] arrivals, [1] generation, [2] error; zero before each launch
   const int32_t* ctl;       // written by the finalize kernel: 1 = decompose
   double* out;              // finalize result buffer
   int64_t evals_off, evecs_off, flags_off;
-  int32_t pa, m;            // analysis columns; m = pa rounded up to even
+  int32_t pa, m;            // analysis columns; m = pa rounded up to a multiple of 16
 };
 // Doubles of scratch jacobi_grid_kernel needs for pa analysis columns (the five arrays above).
 size_t jacobi_scratch_doubles(int pa);
