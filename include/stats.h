@@ -237,6 +237,9 @@ stats_status stats_finalize_warm(stats_ctx* ctx, double* mean, double* cov, doub
 /* stats_finalize for many contexts in one launch (one thread block per context; the
  * FP64 eigen-solver of each block is what a single call costs, so many contexts cost
  * about one call per SM-load instead of one call each).  Synchronises every context.
+ * mean, cov and corr are those of stats_finalize bit for bit; the eigenpairs too below 24
+ * analysis columns, while from 24 columns (where stats_finalize runs its eigen-solver
+ * over the whole GPU) they agree with stats_finalize's to rounding.
  * For context i the caller-owned HOST outputs mean[i], cov[i], corr[i], evals[i],
  * evecs[i] are laid out as in stats_finalize; any of the five arrays may be NULL, and
  * so may any entry.  Outputs of contexts with fewer than two rows are left untouched.

@@ -36,6 +36,9 @@ constexpr int64_t kDefaultChunkRows = int64_t(1) << 24;
 // tens of microseconds) outweigh its faster streaming.  Batches keep the register-fragment
 // launch, which shares those costs across its tables.
 constexpr int64_t kNarrowMinRows = int64_t(1) << 20;
+// Tables of a batched call with 33..64 columns and at least this many rows share one
+// persistent narrow launch; smaller ones stay with the register-fragment launch.
+constexpr int64_t kNarrowBatchMinRows = 4096;
 
 struct ColPlan {
   int k = 0;         // digit bytes
@@ -603,6 +606,30 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
   return STATS_OK;
 }
 
+// The narrow-pass description of one table (its tensor map must be current in c->tmap).
+NarrowTab narrow_table(stats_ctx* c, const void* const* dcols, int64_t nrows) {
+  NarrowTab T{};
+  T.tmap = c->d_tmap;
+  T.base = static_cast<const float*>(dcols[0]);
+  T.ld = (static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0])) / 4;
+  T.shift = c->d_fshift;
+  T.shift_d = c->d_shift;
+  T.acc_s = c->d_fs;
+  T.acc_s_lo = c->d_fs_lo;
+  T.acc_S = c->d_fS;
+  T.acc_S_lo = c->d_fS_lo;
+  T.acc_n = c->d_fn;
+  T.nrows = nrows;
+  T.nfull = nrows / wide_chunk_rows();
+  T.p = c->p;
+  return T;
+}
+
+int narrow_flush_stages(const stats_ctx* c) {
+  const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
+  return std::max(1, flush_rows / narrow_rows_per_stage());  // one chain per stage
+}
+
 stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
   if (!c->shift_set) {
     SplitParams S{};
@@ -612,12 +639,7 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
     CK(c, launch_split_shift(S, c->d_shift, st));
     c->shift_set = true;
   }
-  WideParams W{};
   const int grid = std::max(1, c->sms);
-  W.nunits = 1;
-  W.unit_i[0] = W.unit_j[0] = 0;
-  W.unit_first[0] = 0;
-  W.unit_ctas[0] = grid;
   if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
     if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
     c->d_wide_slots = nullptr;
@@ -626,23 +648,120 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
   }
   if (!c->d_tmap) CK(c, cudaMalloc(&c->d_tmap, sizeof(CUtensorMap)));
   CK(c, cudaMemcpyAsync(c->d_tmap, &c->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
-  W.tmap = c->d_tmap;
-  W.base = static_cast<const float*>(dcols[0]);
-  W.ld = (static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0])) / 4;
-  W.shift = c->d_fshift;
-  W.slots = c->d_wide_slots;
-  W.acc_s = c->d_fs;
-  W.acc_s_lo = c->d_fs_lo;
-  W.acc_S = c->d_fS;
-  W.acc_S_lo = c->d_fS_lo;
-  W.acc_n = c->d_fn;
-  W.status = c->d_status;
-  W.nrows = nrows;
-  W.nfull = nrows / wide_chunk_rows();
-  W.p = c->p;
-  const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
-  W.flush_chains = std::max(1, flush_rows / narrow_rows_per_stage());  // one chain per stage
-  CK(c, launch_narrow(W, c->mode == STATS_BF16X4, grid, st));
+  NarrowParams P{};
+  P.tab0 = narrow_table(c, dcols, nrows);
+  P.nunits = grid;  // the table's stages in grid consecutive ranges, one per CTA
+  P.ntabs = 1;
+  P.slots = c->d_wide_slots;
+  P.status = c->d_status;
+  P.flush_stages = narrow_flush_stages(c);
+  CK(c, launch_narrow(P, c->mode == STATS_BF16X4, grid, st));
+  return STATS_OK;
+}
+
+// Tables of 33..64 FP32 columns of one batched call, one mode: a single persistent narrow
+// launch.  Each table is cut into units of at most U stages, U chosen so that the CTAs get
+// about kNarrowUnitsPerCta units each (a unit runs on one SM: large units would leave the
+// last CTAs finishing alone); units are dealt to CTAs largest first (CTA b takes units b,
+// b + grid, ...), and every unit has its own slot, merged per table in row order.
+constexpr int kNarrowUnitsPerCta = 6;
+constexpr int64_t kNarrowUnitMinStages = 64, kNarrowUnitMaxStages = 16384;
+
+struct NarrowJob {
+  stats_ctx* c;
+  const void* const* cols;
+  int64_t nrows;
+};
+
+struct NarrowWorkspace {
+  void* dev = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t last = nullptr;
+};
+std::mutex g_narrow_mu;
+NarrowWorkspace g_narrow_ws[64];
+
+stats_status run_narrow_batch(const std::vector<NarrowJob>& jobs, bool x4, cudaStream_t st) {
+  if (jobs.empty()) return STATS_OK;
+  stats_ctx* c0 = jobs[0].c;
+  int dev = 0;
+  CK(c0, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return STATS_EINVAL;
+  const int rs = narrow_rows_per_stage();
+  const size_t nt = jobs.size();
+  std::vector<NarrowTab> tabs(nt);
+  std::vector<CUtensorMap> maps(nt);
+  std::vector<int32_t> slot0(nt + 1, 0);
+  std::vector<NarrowUnit> units;
+  std::vector<int> need_shift;
+  int64_t total = 0;
+  for (const NarrowJob& j : jobs) total += (j.nrows + rs - 1) / rs;
+  const int64_t ustages = std::min(kNarrowUnitMaxStages,
+                                   std::max(kNarrowUnitMinStages, total / (int64_t(std::max(1, c0->sms)) *
+                                                                           kNarrowUnitsPerCta)));
+  for (size_t i = 0; i < nt; ++i) {
+    const NarrowJob& j = jobs[i];
+    tabs[i] = narrow_table(j.c, j.cols, j.nrows);
+    maps[i] = j.c->tmap;
+    if (!j.c->shift_set) need_shift.push_back(static_cast<int>(i));
+    const int64_t nst = (j.nrows + rs - 1) / rs;
+    const int64_t nu = (nst + ustages - 1) / ustages;
+    slot0[i + 1] = slot0[i] + static_cast<int32_t>(nu);
+    for (int64_t u = 0; u < nu; ++u) {
+      NarrowUnit U{};
+      U.st0 = u * nst / nu;
+      U.nst = static_cast<int32_t>((u + 1) * nst / nu - U.st0);
+      U.tab = static_cast<int32_t>(i);
+      U.slot = slot0[i] + static_cast<int32_t>(u);
+      units.push_back(U);
+    }
+  }
+  std::stable_sort(units.begin(), units.end(), [](const NarrowUnit& a, const NarrowUnit& b) { return a.nst > b.nst; });
+  const int nunits = static_cast<int>(units.size());
+  const int grid = std::min(nunits, std::max(1, c0->sms));
+  const size_t off_maps = ((nt * sizeof(NarrowTab) + 255) / 256) * 256;
+  const size_t off_units = off_maps + nt * sizeof(CUtensorMap);  // 128-byte maps, 64-byte aligned
+  const size_t off_slot0 = off_units + (((units.size() * sizeof(NarrowUnit)) + 255) / 256) * 256;
+  const size_t off_which = off_slot0 + (((nt + 1) * sizeof(int32_t) + 255) / 256) * 256;
+  const size_t off_slots = off_which + ((need_shift.size() * sizeof(int) + 255) / 256) * 256;
+  const size_t need = off_slots + static_cast<size_t>(nunits) * kWideSlotPairs * 2 * sizeof(float);
+  std::lock_guard<std::mutex> lk(g_narrow_mu);
+  NarrowWorkspace& ws = g_narrow_ws[dev];
+  if (!ws.last) CK(c0, cudaEventCreateWithFlags(&ws.last, cudaEventDisableTiming));
+  CK(c0, cudaStreamWaitEvent(st, ws.last, 0));  // the previous user of the workspace is done
+  if (ws.bytes < need) {
+    if (ws.dev) CK(c0, cudaFree(ws.dev));  // synchronises the device
+    ws.dev = nullptr;
+    ws.bytes = 0;
+    CK(c0, cudaMalloc(&ws.dev, need));
+    ws.bytes = need;
+  }
+  char* base = static_cast<char*>(ws.dev);
+  for (size_t i = 0; i < nt; ++i) tabs[i].tmap = base + off_maps + i * sizeof(CUtensorMap);
+  CK(c0, cudaMemcpyAsync(base, tabs.data(), nt * sizeof(NarrowTab), cudaMemcpyHostToDevice, st));
+  CK(c0, cudaMemcpyAsync(base + off_maps, maps.data(), nt * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  CK(c0, cudaMemcpyAsync(base + off_units, units.data(), units.size() * sizeof(NarrowUnit), cudaMemcpyHostToDevice,
+                         st));
+  CK(c0, cudaMemcpyAsync(base + off_slot0, slot0.data(), (nt + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (!need_shift.empty()) {
+    CK(c0, cudaMemcpyAsync(base + off_which, need_shift.data(), need_shift.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+    CK(c0, launch_narrow_shift(reinterpret_cast<const NarrowTab*>(base), reinterpret_cast<const int*>(base + off_which),
+                               static_cast<int>(need_shift.size()), st));
+    for (int i : need_shift) jobs[i].c->shift_set = true;
+  }
+  NarrowParams P{};
+  P.tabs = reinterpret_cast<const NarrowTab*>(base);
+  P.units = reinterpret_cast<const NarrowUnit*>(base + off_units);
+  P.tab_slot0 = reinterpret_cast<const int32_t*>(base + off_slot0);
+  P.slots = reinterpret_cast<float*>(base + off_slots);
+  P.status = c0->d_status;
+  P.nunits = nunits;
+  P.ntabs = static_cast<int32_t>(nt);
+  P.flush_stages = narrow_flush_stages(c0);
+  for (const NarrowJob& j : jobs) P.flush_stages = std::min(P.flush_stages, narrow_flush_stages(j.c));
+  CK(c0, launch_narrow(P, x4, grid, st));
+  CK(c0, cudaEventRecord(ws.last, st));
   return STATS_OK;
 }
 
@@ -1367,6 +1486,7 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
   // up to 64 columns share the register-fragment launch, wider ones the tiled launch
   std::vector<int> split_idx;
   std::vector<Gram32Job> g32;
+  std::vector<NarrowJob> narrow[2];  // by mode: BF16x3, BF16x4
   for (int t = 0; t < ntables; ++t) {
     stats_ctx* c = ctxs[t];
     stats_status s = check_sticky(c);
@@ -1376,7 +1496,9 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
-      if (c->p <= 64) {
+      if (c->p > 32 && c->p <= 64 && nrows[t] >= kNarrowBatchMinRows && narrow_eligible(c, dcols[t], nrows[t])) {
+        narrow[c->mode == STATS_BF16X4 ? 1 : 0].push_back({c, dcols[t], nrows[t]});
+      } else if (c->p <= 64) {
         g32.push_back({c, dcols[t], nrows[t]});
       } else if (wide_eligible(c, dcols[t], nrows[t])) {
         s = launch_pass(c, dcols[t], nrows[t], st);  // one tcgen05 launch per wide table
@@ -1391,6 +1513,10 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
   }
   if (!g32.empty()) {
     stats_status s = run_gram32(g32, st);
+    if (s != STATS_OK) return s;
+  }
+  for (int x4 = 0; x4 < 2; ++x4) {
+    stats_status s = run_narrow_batch(narrow[x4], x4 == 1, st);
     if (s != STATS_OK) return s;
   }
   if (split_idx.empty()) return STATS_OK;

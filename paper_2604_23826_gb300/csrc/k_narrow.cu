@@ -56,22 +56,34 @@ constexpr int kNTmemCols = 256;
 constexpr int kNFold = 16;                        // stages of FP32 partial sums of l^2 per fold
 constexpr int kNSlotStride = 128;                 // pairs per slot row (the wide pass's slot layout)
 
+__device__ __forceinline__ NarrowUnit narrow_unit(const NarrowParams& P, int u) {
+  if (P.units) return P.units[u];
+  const int64_t nst = (P.tab0.nrows + kNRows - 1) / kNRows;
+  const int64_t a = u * nst / P.nunits, b = (u + 1) * nst / P.nunits;
+  NarrowUnit U;
+  U.st0 = a;
+  U.nst = static_cast<int32_t>(b - a);
+  U.tab = 0;
+  U.slot = u;
+  U.pad = 0;
+  return U;
+}
+__device__ __forceinline__ const NarrowTab& narrow_tab(const NarrowParams& P, int t) {
+  return P.tabs ? P.tabs[t] : P.tab0;
+}
+
 template <bool X4>
-__global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_constant__ WideParams P) {
+__global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_constant__ NarrowParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t f_full[kNStages], c_full[kNStages], f_empty[kNStages], d_full[2], d_empty[2],
       fin;
   __shared__ uint32_t s_tmem;
   __shared__ volatile unsigned int s_dead;
   __shared__ int s_rows[kNStages];
-  __shared__ float s_piv[kNCols];
 
   constexpr int NB = X4 ? 128 : 64;  // accumulator columns of a chain
   constexpr uint32_t kIdesc = idesc_bf16(128, NB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int G = gridDim.x, q0 = blockIdx.x;
-  const int64_t nst = (P.nrows + kNRows - 1) / kNRows;
-  const int64_t my = q0 < nst ? (nst - 1 - q0) / G + 1 : 0;  // stages of this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kNStages; ++s) {
@@ -87,7 +99,6 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     s_dead = 0;
     fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < kNCols; i += kNThreads) s_piv[i] = i < P.p ? P.shift[i] : 0.f;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(kNTmemCols)
@@ -101,34 +112,42 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
   // registers: warpgroup 3 (the epilogue) takes 200 per thread, warpgroups 0-2 give up to 104
   if (warp < 12) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kNRegsLow));
 
+  // Every role walks the same units (u = blockIdx.x, + gridDim.x, ...) and, in each, the same
+  // stages; the stage ring and the two TMEM buffers run on across units.
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     // (the whole warp runs the loop; one lane waits, one elected lane issues)
     int s = 0;
     uint32_t ph = 0;
-    int64_t k = 0;
-    for (; k < my; ++k) {
-      const int64_t st = q0 + k * G;
-      const bool ok = __shfl_sync(
-          0xffffffffu, lane == 0 ? (k < kNStages || wait_live(&f_empty[s], ph ^ 1u, &s_dead)) : false, 0);
-      if (!ok) {
-        if (lane == 0) record_timeout(&s_dead, P.status);
-        break;
-      }
-      if (elect_one()) {
-        s_rows[s] = static_cast<int>(min(static_cast<int64_t>(kNRows), P.nrows - st * kNRows));
-        mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(kNStageBytes));
-        tma_load_3d(smem + static_cast<size_t>(s) * kNStageBytes, P.tmap, 0, static_cast<int>(st * kNChunks), 0,
-                    &f_full[s]);
-      }
-      __syncwarp();
-      if (++s == kNStages) {
-        s = 0;
-        ph ^= 1u;
+    int64_t issued = 0;
+    bool live = true;
+    for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
+      const NarrowUnit U = narrow_unit(P, u);
+      const NarrowTab& T = narrow_tab(P, U.tab);
+      for (int k = 0; k < U.nst; ++k, ++issued) {
+        const int64_t st = U.st0 + k;
+        const bool ok = __shfl_sync(
+            0xffffffffu, lane == 0 ? (issued < kNStages || wait_live(&f_empty[s], ph ^ 1u, &s_dead)) : false, 0);
+        if (!ok) {
+          if (lane == 0) record_timeout(&s_dead, P.status);
+          live = false;
+          break;
+        }
+        if (elect_one()) {
+          s_rows[s] = static_cast<int>(min(static_cast<int64_t>(kNRows), T.nrows - st * kNRows));
+          mbar_arrive_expect_tx(&f_full[s], static_cast<uint32_t>(kNStageBytes));
+          tma_load_3d(smem + static_cast<size_t>(s) * kNStageBytes, T.tmap, 0, static_cast<int>(st * kNChunks), 0,
+                      &f_full[s]);
+        }
+        __syncwarp();
+        if (++s == kNStages) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
     }
     if (lane == 0) {
-      for (int d = 0; d < kNStages && d < k; ++d) {  // no copy in flight at exit
+      for (int d = 0; d < kNStages && d < issued; ++d) {  // no copy in flight at exit
         int sk = s - 1 - d;
         uint32_t pk = ph;
         while (sk < 0) {
@@ -145,40 +164,46 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     // issues the tcgen05 instructions.
     int s = 0, bd = 0;
     uint32_t ph = 0, phd = 0;
-    for (int64_t k = 0; k < my; ++k) {
-      // stage k: converted, and its TMEM buffer drained by the epilogue (stage k - 2)
-      const bool ok = __shfl_sync(0xffffffffu,
-                                  lane == 0 ? (wait_live(&c_full[s], ph, &s_dead) &&
-                                               (k < 2 || wait_live(&d_empty[bd], phd ^ 1u, &s_dead)))
-                                            : false,
-                                  0);
-      if (!ok) {
-        if (lane == 0) record_timeout(&s_dead, P.status);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + static_cast<size_t>(s) * kNStageBytes);
-      const uint32_t dt = tmem + static_cast<uint32_t>(bd * 128);
-      // one fresh chain per stage: K step ks = K groups 2 ks and 2 ks + 1; A = the stacked
-      // operand, B = the same (BF16x4) or its h rows.  The epilogue frees the stage once this
-      // commit has arrived.
-      if (elect_one()) {
-#pragma unroll
-        for (int ks = 0; ks < kNRows / 16; ++ks) {
-          const uint64_t a = desc<kNLbo, kNSbo>(base + ks * 2 * kNLbo);
-          const uint64_t b = X4 ? a : desc<kNLbo, 2 * kNSbo>(base + ks * 2 * kNLbo);
-          mma_bf16(dt, a, b, kIdesc, ks);
+    int64_t chains = 0;
+    bool live = true;
+    for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
+      const int nst = narrow_unit(P, u).nst;
+      for (int k = 0; k < nst; ++k, ++chains) {
+        // stage converted, and its TMEM buffer drained by the epilogue (two chains back)
+        const bool ok = __shfl_sync(0xffffffffu,
+                                    lane == 0 ? (wait_live(&c_full[s], ph, &s_dead) &&
+                                                 (chains < 2 || wait_live(&d_empty[bd], phd ^ 1u, &s_dead)))
+                                              : false,
+                                    0);
+        if (!ok) {
+          if (lane == 0) record_timeout(&s_dead, P.status);
+          live = false;
+          break;
         }
-        umma_commit(&d_full[bd]);
-      }
-      __syncwarp();
-      if (++bd == 2) {
-        bd = 0;
-        phd ^= 1u;
-      }
-      if (++s == kNStages) {
-        s = 0;
-        ph ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem + static_cast<size_t>(s) * kNStageBytes);
+        const uint32_t dt = tmem + static_cast<uint32_t>(bd * 128);
+        // one fresh chain per stage: K step ks = K groups 2 ks and 2 ks + 1; A = the stacked
+        // operand, B = the same (BF16x4) or its h rows.  The epilogue frees the stage once this
+        // commit has arrived.
+        if (elect_one()) {
+#pragma unroll
+          for (int ks = 0; ks < kNRows / 16; ++ks) {
+            const uint64_t a = desc<kNLbo, kNSbo>(base + ks * 2 * kNLbo);
+            const uint64_t b = X4 ? a : desc<kNLbo, 2 * kNSbo>(base + ks * 2 * kNLbo);
+            mma_bf16(dt, a, b, kIdesc, ks);
+          }
+          umma_commit(&d_full[bd]);
+        }
+        __syncwarp();
+        if (++bd == 2) {
+          bd = 0;
+          phd ^= 1u;
+        }
+        if (++s == kNStages) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
     }
     if (elect_one()) umma_commit(&fin);  // every issued MMA completes before the tensor memory is released
@@ -195,106 +220,113 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     const int cw = warp - 4;
     const int sub = lane & 7, qd = lane >> 3;
     const int c = 8 * cw + sub;
-    float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;  // column sums of r and l^2, (hi, lo)
-    float2 pq = make_float2(0.f, 0.f);
-    int since = 0;
-    const int64_t tail = P.nrows - P.nfull * kNChunk;
-    const float ncp = -s_piv[c];
-    const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+    const float2 m1 = make_float2(-1.f, -1.f);
     int s = 0;
     uint32_t ph = 0;
-    for (int64_t k = 0; k < my; ++k) {
-      const bool ok = __all_sync(0xffffffffu, wait_live(&f_full[s], ph, &s_dead));
-      if (!ok) {
-        if (lane == 0) record_timeout(&s_dead, P.status);
-        break;
-      }
-      const int64_t st = q0 + k * G;
-      const int rows = s_rows[s];
-      uint8_t* base = smem + static_cast<size_t>(s) * kNStageBytes;
-      const int64_t jt = P.nfull - st * kNChunks;  // chunk of the stage holding the tail, if 0 or 1
-      if (tail > 0 && (jt == 0 || jt == 1)) {
-        if (lane < 8 && 8 * cw + lane < P.p) {
-          const int cc = 8 * cw + lane;
-          const int L = 2 * cc + static_cast<int>(jt);
-          const float* src = P.base + static_cast<int64_t>(cc) * P.ld + P.nfull * kNChunk;
-          for (int t = 0; t < static_cast<int>(tail); ++t)
-            *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
+    bool live = true;
+    for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
+      const NarrowUnit U = narrow_unit(P, u);
+      const NarrowTab& T = narrow_tab(P, U.tab);
+      float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;  // column sums of r and l^2, (hi, lo)
+      float2 pq = make_float2(0.f, 0.f);
+      int since = 0;
+      const int64_t tail = T.nrows - T.nfull * kNChunk;
+      const float ncp = c < T.p ? -T.shift[c] : 0.f;
+      const float2 np = make_float2(ncp, ncp);
+      for (int k = 0; k < U.nst; ++k) {
+        const bool ok = __all_sync(0xffffffffu, wait_live(&f_full[s], ph, &s_dead));
+        if (!ok) {
+          if (lane == 0) record_timeout(&s_dead, P.status);
+          live = false;
+          break;
         }
-        __syncwarp();
-      }
-      float4 x[2][2];
+        const int64_t st = U.st0 + k;
+        const int rows = s_rows[s];
+        uint8_t* base = smem + static_cast<size_t>(s) * kNStageBytes;
+        const int64_t jt = T.nfull - st * kNChunks;  // chunk of the stage holding the tail, if 0 or 1
+        if (tail > 0 && (jt == 0 || jt == 1)) {
+          if (lane < 8 && 8 * cw + lane < T.p) {
+            const int cc = 8 * cw + lane;
+            const int L = 2 * cc + static_cast<int>(jt);
+            const float* src = T.base + static_cast<int64_t>(cc) * T.ld + T.nfull * kNChunk;
+            for (int t = 0; t < static_cast<int>(tail); ++t)
+              *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
+          }
+          __syncwarp();
+        }
+        float4 x[2][2];
 #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int L = 2 * c + ((sub >> 2) ^ it);
-        x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
-        x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
-      }
-      __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
+        for (int it = 0; it < 2; ++it) {
+          const int L = 2 * c + ((sub >> 2) ^ it);
+          x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+          x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+        }
+        __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
 #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int j = (sub >> 2) ^ it;
-        const int row = kNChunk * j + 8 * qd;
-        float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
-                       __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
-                       __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
-                       __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
-        if (rows < kNRows) {
+        for (int it = 0; it < 2; ++it) {
+          const int j = (sub >> 2) ^ it;
+          const int row = kNChunk * j + 8 * qd;
+          float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
+                         __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
+                         __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
+                         __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
+          if (rows < kNRows) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (row + 2 * q >= rows) r[q].x = 0.f;
+              if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+            }
+          }
+          uint32_t h[4], l[4];
+          float2 e[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            if (row + 2 * q >= rows) r[q].x = 0.f;
-            if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+            h[q] = pack_bf16x2(r[q].x, r[q].y);
+            e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+            l[q] = pack_bf16x2(e[q].x, e[q].y);
           }
-        }
-        uint32_t h[4], l[4];
-        float2 e[4];
+          const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
+          two_sum(sh, sl, a.x + a.y);
+          two_sum(sh, sl, b.x + b.y);
+          if (!X4) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          h[q] = pack_bf16x2(r[q].x, r[q].y);
-          e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
-          l[q] = pack_bf16x2(e[q].x, e[q].y);
+            for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
+          }
+          const int kk = 4 * j + qd;
+          uint8_t* hp = base + 2 * cw * kNSbo + kk * kNLbo + sub * 16;
+          *reinterpret_cast<uint4*>(hp) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(hp + kNSbo) = make_uint4(l[0], l[1], l[2], l[3]);
         }
-        const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
-        two_sum(sh, sl, a.x + a.y);
-        two_sum(sh, sl, b.x + b.y);
-        if (!X4) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c_full[s]);
+        if (!X4 && ++since == kNFold) {
+          since = 0;
+          two_sum(qh, ql, pq.x + pq.y);
+          pq = make_float2(0.f, 0.f);
         }
-        const int kk = 4 * j + qd;
-        uint8_t* hp = base + 2 * cw * kNSbo + kk * kNLbo + sub * 16;
-        *reinterpret_cast<uint4*>(hp) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(hp + kNSbo) = make_uint4(l[0], l[1], l[2], l[3]);
+        if (++s == kNStages) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&c_full[s]);
-      if (!X4 && ++since == kNFold) {
-        since = 0;
-        two_sum(qh, ql, pq.x + pq.y);
-        pq = make_float2(0.f, 0.f);
-      }
-      if (++s == kNStages) {
-        s = 0;
-        ph ^= 1u;
-      }
-    }
-    two_sum(qh, ql, pq.x + pq.y);
-    // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
+      two_sum(qh, ql, pq.x + pq.y);
+      // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
 #pragma unroll
-    for (int d = 8; d < 32; d <<= 1) {
-      const float oh_ = __shfl_xor_sync(0xffffffffu, sh, d), ol_ = __shfl_xor_sync(0xffffffffu, sl, d);
-      const float oq_ = __shfl_xor_sync(0xffffffffu, qh, d), oql = __shfl_xor_sync(0xffffffffu, ql, d);
-      two_sum(sh, sl, oh_);
-      sl += ol_;
-      two_sum(qh, ql, oq_);
-      ql += oql;
-    }
-    if (lane < 8) {
-      float2* cs = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
-                   128 * kNSlotStride;
-      cs[c] = make_float2(sh, sl);
-      cs[128 + c] = make_float2(qh, ql);
+      for (int d = 8; d < 32; d <<= 1) {
+        const float oh_ = __shfl_xor_sync(0xffffffffu, sh, d), ol_ = __shfl_xor_sync(0xffffffffu, sl, d);
+        const float oq_ = __shfl_xor_sync(0xffffffffu, qh, d), oql = __shfl_xor_sync(0xffffffffu, ql, d);
+        two_sum(sh, sl, oh_);
+        sl += ol_;
+        two_sum(qh, ql, oq_);
+        ql += oql;
+      }
+      if (lane < 8) {
+        float2* cs = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(U.slot) * kWideSlotPairs +
+                     128 * kNSlotStride;
+        cs[c] = make_float2(sh, sl);
+        cs[128 + c] = make_float2(qh, ql);
+      }
     }
   } else if (warp >= 12) {
     // ---------------------------------------------------------------- epilogue (warpgroup 3)
@@ -304,64 +336,70 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     float acc[kNCols];
 #pragma unroll
     for (int i = 0; i < kNCols; ++i) acc[i] = 0.f;
-    float2* slot = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(blockIdx.x) * kWideSlotPairs +
-                   static_cast<size_t>(m) * kNSlotStride;
-    bool fresh = true;
-    int since = 0;
-    auto flush = [&]() {
-#pragma unroll
-      for (int i0 = 0; i0 < kNCols; i0 += 8) {
-        float2 hl[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(slot + i0 + k);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          two_sum(hl[k].x, hl[k].y, acc[i0 + k]);
-          acc[i0 + k] = 0.f;
-          __stcg(slot + i0 + k, hl[k]);
-        }
-        asm volatile("" ::: "memory");
-      }
-      fresh = false;
-    };
     int bd = 0, se = 0;
     uint32_t phd = 0;
-    for (int64_t k = 0; k < my; ++k) {
-      const bool ok = __all_sync(0xffffffffu, wait_live(&d_full[bd], phd, &s_dead));  // .sync.aligned loads follow
-      if (!ok) {
-        if (lane == 0) record_timeout(&s_dead, P.status);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // the stage's MMAs have completed: its shared memory goes back to the producer
-      if (warp == 12 && lane == 0) mbar_arrive(&f_empty[se]);
-      if (++se == kNStages) se = 0;
-      const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * 128);
+    bool live = true;
+    for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
+      const NarrowUnit U = narrow_unit(P, u);
+      float2* slot = reinterpret_cast<float2*>(P.slots) + static_cast<size_t>(U.slot) * kWideSlotPairs +
+                     static_cast<size_t>(m) * kNSlotStride;
+      bool fresh = true;
+      int since = 0;
+      auto flush = [&]() {
 #pragma unroll
-      for (int c0 = 0; c0 < NB; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
-        if (X4) {  // columns 16 g .. 16 g + 7: h of columns 8 g + i; the next 8: their l
+        for (int i0 = 0; i0 < kNCols; i0 += 8) {
+          float2 hl[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc[c0 / 2 + i] += v[i] + v[8 + i];
-        } else {
+          for (int k = 0; k < 8; ++k) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(slot + i0 + k);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+          for (int k = 0; k < 8; ++k) {
+            two_sum(hl[k].x, hl[k].y, acc[i0 + k]);
+            acc[i0 + k] = 0.f;
+            __stcg(slot + i0 + k, hl[k]);
+          }
+          asm volatile("" ::: "memory");
+        }
+        fresh = false;
+      };
+      for (int k = 0; k < U.nst; ++k) {
+        const bool ok = __all_sync(0xffffffffu, wait_live(&d_full[bd], phd, &s_dead));  // .sync.aligned loads follow
+        if (!ok) {
+          if (lane == 0) record_timeout(&s_dead, P.status);
+          live = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the stage's MMAs have completed: its shared memory goes back to the producer
+        if (warp == 12 && lane == 0) mbar_arrive(&f_empty[se]);
+        if (++se == kNStages) se = 0;
+        const uint32_t taddr =
+            tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * 128);
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+          float v[16];
+          tmem_ld16(taddr + c0, v);
+          if (X4) {  // columns 16 g .. 16 g + 7: h of columns 8 g + i; the next 8: their l
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[c0 / 2 + i] += v[i] + v[8 + i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d_empty[bd]);
+        if (++bd == 2) {
+          bd = 0;
+          phd ^= 1u;
+        }
+        if (++since >= P.flush_stages) {
+          since = 0;
+          flush();
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&d_empty[bd]);
-      if (++bd == 2) {
-        bd = 0;
-        phd ^= 1u;
-      }
-      if (++since >= P.flush_chains) {  // flush_chains counts stages here
-        since = 0;
-        flush();
-      }
+      flush();  // every unit's slot is written, also when it had no stage
     }
-    flush();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -371,8 +409,8 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
   }
 }
 
-// Sum of slot entry idx over CTAs [q0, q1) into (h, l), eight loads in flight (the entries of
-// consecutive CTAs are 133 KB apart: each load is its own L2 round trip).
+// Sum of slot entry idx over slots [q0, q1) into (h, l), eight loads in flight (consecutive
+// slots are 133 KB apart: each load is its own L2 round trip).
 __device__ __forceinline__ void sum_slots(const float2* slots, int idx, int q0, int q1, float& h, float& l) {
   for (int q = q0; q < q1; q += 8) {
     float2 x[8];
@@ -395,17 +433,22 @@ __device__ __forceinline__ void dd_add(double* hi, double* lo, int64_t e, float 
   hi[e] = s;
 }
 
-// The CTA slots into the context's double-double accumulators.  Block m (< p) takes row m of
-// S, block p the column sums; thread (n, quarter) adds CTAs [quarter G / 4, (quarter + 1) G / 4)
-// and the quarters are then combined in order, so the result depends on the grid only.
+// A table's unit slots into its context's double-double accumulators.  Block (m, t): table t,
+// row m (< p) of S, or (m = p) the column sums; thread (n, quarter) adds a quarter of the
+// table's slots and the quarters are then combined in order, so the result depends on the
+// units only.
 template <bool X4>
-__global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant__ WideParams P, int grid) {
+__global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant__ NarrowParams P) {
   __shared__ float2 part[4][kNCols];
-  const int p = P.p;
+  const int t = blockIdx.y;
+  const NarrowTab& T = narrow_tab(P, t);
+  const int p = T.p;
+  const int m = blockIdx.x;
+  if (m > p) return;  // the whole block
+  const int u0 = P.tab_slot0 ? P.tab_slot0[t] : 0, u1 = P.tab_slot0 ? P.tab_slot0[t + 1] : P.nunits;
   const float2* slots = reinterpret_cast<const float2*>(P.slots);
   const int n = threadIdx.x & (kNCols - 1), qq = threadIdx.x / kNCols;
-  const int q0 = qq * grid / 4, q1 = (qq + 1) * grid / 4;
-  const int m = blockIdx.x;
+  const int q0 = u0 + qq * (u1 - u0) / 4, q1 = u0 + (qq + 1) * (u1 - u0) / 4;
   float h = 0.f, l = 0.f;
   if (m < p) {
     if (n >= m && n < p) {
@@ -428,22 +471,31 @@ __global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant
       l += part[k][n].y;
     }
     if (m < p && n >= m && n < p)
-      dd_add(P.acc_S, P.acc_S_lo, static_cast<int64_t>(m) * p - static_cast<int64_t>(m) * (m - 1) / 2 + (n - m), h, l);
+      dd_add(T.acc_S, T.acc_S_lo, static_cast<int64_t>(m) * p - static_cast<int64_t>(m) * (m - 1) / 2 + (n - m), h, l);
     else if (m == p && n < p)
-      dd_add(P.acc_s, P.acc_s_lo, n, h, l);
-    if (m == p && n == 0) *P.acc_n += P.nrows;
+      dd_add(T.acc_s, T.acc_s_lo, n, h, l);
+    if (m == p && n == 0) *T.acc_n += T.nrows;
+  }
+}
+
+__global__ void narrow_shift_kernel(const NarrowTab* __restrict__ tabs, const int* __restrict__ which) {
+  const NarrowTab& T = tabs[which[blockIdx.x]];
+  for (int j = threadIdx.x; j < T.p; j += blockDim.x) {
+    const float v = T.base[static_cast<int64_t>(j) * T.ld];
+    T.shift[j] = v;
+    T.shift_d[j] = static_cast<double>(v);
   }
 }
 
 template <bool X4>
-cudaError_t launch_n(const WideParams& P, int grid, cudaStream_t st) {
+cudaError_t launch_n(const NarrowParams& P, int grid, cudaStream_t st) {
   const int smem = kNStages * kNStageBytes;
   cudaError_t e = cudaFuncSetAttribute(narrow_kernel<X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   narrow_kernel<X4><<<grid, kNThreads, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  narrow_merge_kernel<X4><<<P.p + 1, 256, 0, st>>>(P, grid);
+  narrow_merge_kernel<X4><<<dim3(kNCols + 1, P.tabs ? P.ntabs : 1), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -452,8 +504,15 @@ cudaError_t launch_n(const WideParams& P, int grid, cudaStream_t st) {
 int narrow_cols() { return kNCols; }
 int narrow_rows_per_stage() { return kNRows; }
 
-cudaError_t launch_narrow(const WideParams& P, bool x4, int grid, cudaStream_t st) {
+cudaError_t launch_narrow(const NarrowParams& P, bool x4, int grid, cudaStream_t st) {
+  if (grid < 1 || P.nunits < 1 || (P.tabs && (P.ntabs < 1 || !P.units || !P.tab_slot0))) return cudaErrorInvalidValue;
   return x4 ? launch_n<true>(P, grid, st) : launch_n<false>(P, grid, st);
+}
+
+cudaError_t launch_narrow_shift(const NarrowTab* tabs, const int* which, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  narrow_shift_kernel<<<count, 64, 0, st>>>(tabs, which);
+  return cudaGetLastError();
 }
 
 }  // namespace ss

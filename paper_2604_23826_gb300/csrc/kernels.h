@@ -202,7 +202,41 @@ cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st)
 // WideParams with a single unit (0, 0) of `grid` CTAs, tmap boxed (32, 2, 64).
 int narrow_cols();
 int narrow_rows_per_stage();
-cudaError_t launch_narrow(const WideParams& P, bool x4, int grid, cudaStream_t st);
+// A table of a narrow launch: a [p, ld] block of FP32 columns, 33 <= p <= 64.
+struct NarrowTab {
+  const void* tmap;          // device copy of its 3D tensor map: dims (32, nrows / 32, p), box (32, 2, 64)
+  const float* base;         // column 0; column j at base + j * ld
+  float* shift;              // p pivots (FP32, device)
+  double* shift_d;           // the same in FP64 (the ctx's shift vector)
+  double* acc_s;             // ctx accumulators (shifted), double-double
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+  int64_t nrows, ld, nfull;  // nfull: whole 32-row chunks; the rest is read with plain loads
+  int32_t p, pad;
+};
+// A unit of work: 64-row stages [st0, st0 + nst) of table tab, reduced into slot `slot`
+// (a table's units own consecutive slots, in row order).
+struct NarrowUnit {
+  int64_t st0;
+  int32_t nst, tab, slot, pad;
+};
+struct NarrowParams {
+  NarrowTab tab0;            // the table of a single-table launch (tabs == nullptr)
+  const NarrowTab* tabs;     // ntabs tables (device), or nullptr
+  const NarrowUnit* units;   // nunits units in launch order (device), or nullptr: tab0's stages cut
+                             // into nunits consecutive ranges, unit u in slot u
+  const int32_t* tab_slot0;  // ntabs + 1 entries: table t's slots are [tab_slot0[t], tab_slot0[t + 1])
+  float* slots;              // one slot of kWideSlotPairs pairs per unit
+  unsigned int* status;      // device status word (one per launch: the first table's ctx)
+  int32_t nunits, ntabs;
+  int32_t flush_stages;      // 64-row stages between FP32 -> (hi, lo) flushes
+};
+// CTA b takes units b, b + grid, ...; then one merge block per (row of S or column sums, table).
+cudaError_t launch_narrow(const NarrowParams& P, bool x4, int grid, cudaStream_t st);
+// Pivots (the first row) of tables which[0 .. count) of a device table list.
+cudaError_t launch_narrow_shift(const NarrowTab* tabs, const int* which, int count, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // CUDA-core comparators for any width: FP64 (raw / shifted) and FP32-core.

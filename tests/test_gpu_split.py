@@ -440,8 +440,10 @@ def test_wide_tcgen05_reproducible_and_ragged():
 
 # --------------------------------------------------------------------------- batched finalize
 def test_finalize_batched_matches_single():
-    """Many contexts of different widths and modes finalized in one launch: identical to
-    finalizing each alone; a context with one row is reported and skipped."""
+    """Many contexts of different widths and modes finalized in one launch: mean, cov and corr
+    identical to finalizing each alone, and so are the eigenpairs below 24 analysis columns;
+    from 24 columns a single finalize takes the grid-wide eigen-solver and the batched one the
+    one-block solver, which agree to rounding.  A context with one row is reported and skipped."""
     rng = np.random.default_rng(5)
     ctxs, singles = [], []
     for t, (p, mode) in enumerate([(8, G.STATS_BF16X4), (16, G.STATS_BF16X3), (33, G.STATS_BF16X4),
@@ -458,11 +460,51 @@ def test_finalize_batched_matches_single():
         singles = [G.stats_finalize(c, pca_on) for c in ctxs]
         batched = G.stats_finalize_batched(ctxs, pca_on)
         for a, b in zip(singles, batched):
-            for f in ("mean", "cov", "corr", "evals", "evecs"):
+            for f in ("mean", "cov", "corr"):
                 assert np.array_equal(getattr(a, f), getattr(b, f)), f
+            pa = len(a.evals)
+            if pa < 24:
+                assert np.array_equal(a.evals, b.evals) and np.array_equal(a.evecs, b.evecs)
+                continue
+            scale = np.abs(b.evals).max()
+            assert np.abs(a.evals - b.evals).max() <= 2e-15 * pa * scale
+            gaps = np.abs(np.diff(b.evals))
+            for k in range(pa):
+                sep = min(gaps[k - 1] if k > 0 else np.inf, gaps[k] if k < len(gaps) else np.inf)
+                if sep > 1e-6 * scale:
+                    assert np.abs(a.evecs[k] - b.evecs[k]).max() <= 1e-8, k
     one = G.stats_init(G.Config([G.STATS_F32] * 8, G.STATS_BF16X4, [0] * 8))
     G.stats_accumulate(one, [torch.ones(1, device="cuda") for _ in range(8)], 1)
     with pytest.raises(G.StatsError):
         G.stats_finalize_batched(ctxs[:2] + [one])
     for c in ctxs + [one]:
         c.close()
+
+
+@pytest.mark.parametrize("mode", [G.STATS_BF16X3, G.STATS_BF16X4])
+def test_narrow_batch_persistent_launch(mode):
+    """Tables of 33..64 columns in one batched call share one persistent tcgen05 launch (units of
+    at most 2^20 rows, dealt largest first, one slot each, merged per table in row order):
+    every table against the oracle, against its own single-table call, and the batch rerun
+    bit for bit.  Sizes: several units per table with a ragged tail, one unit, just above the
+    batch threshold."""
+    specs = [(2_100_003, 64), (300_001, 40), (4_096, 33), (70_000, 64), (1_048_577, 48)]
+    tabs = [independent_table(1200 + t, n, p) for t, (n, p) in enumerate(specs)]
+    blocks = [block_cols(X) for X in tabs]
+    mk = lambda X: G.stats_init(G.Config([G.STATS_F32] * X.shape[1], mode, [0] * X.shape[1]))  # noqa: E731
+    ctxs = [mk(X) for X in tabs]
+    again = [mk(X) for X in tabs]
+    rows = [X.shape[0] for X in tabs]
+    G.stats_accumulate_batched(ctxs, [b[1] for b in blocks], rows)
+    G.stats_accumulate_batched(again, [b[1] for b in blocks], rows)
+    for X, c, c2, (blk, cols) in zip(tabs, ctxs, again, blocks):
+        p = X.shape[1]
+        cov = O.cov_twopass_columns([X[:, j].astype(np.float64) for j in range(p)])
+        a = G.stats_finalize(c)
+        assert rel_fro(a.cov, cov) < 2e-6
+        r1, r2 = G.stats_raw(c), G.stats_raw(c2)
+        assert np.array_equal(r1.S, r2.S) and np.array_equal(r1.s, r2.s) and r1.n == r2.n == X.shape[0]
+        _, single = run_cols(cols, X.shape[0], mode)
+        assert rel_fro(a.cov, single.cov) < 1e-6
+        c.close()
+        c2.close()
