@@ -433,17 +433,17 @@ __device__ __forceinline__ void dd_add(double* hi, double* lo, int64_t e, float 
   hi[e] = s;
 }
 
-// A table's unit slots into its context's double-double accumulators.  Block (m, t): table t,
+// A table's unit slots into its context's double-double accumulators.  Block (t, m): table t,
 // row m (< p) of S, or (m = p) the column sums; thread (n, quarter) adds a quarter of the
 // table's slots and the quarters are then combined in order, so the result depends on the
 // units only.
 template <bool X4>
 __global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant__ NarrowParams P) {
   __shared__ float2 part[4][kNCols];
-  const int t = blockIdx.y;
+  const int t = blockIdx.x;
   const NarrowTab& T = narrow_tab(P, t);
   const int p = T.p;
-  const int m = blockIdx.x;
+  const int m = blockIdx.y;
   if (m > p) return;  // the whole block
   const int u0 = P.tab_slot0 ? P.tab_slot0[t] : 0, u1 = P.tab_slot0 ? P.tab_slot0[t + 1] : P.nunits;
   const float2* slots = reinterpret_cast<const float2*>(P.slots);
@@ -495,7 +495,7 @@ cudaError_t launch_n(const NarrowParams& P, int grid, cudaStream_t st) {
   narrow_kernel<X4><<<grid, kNThreads, smem, st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  narrow_merge_kernel<X4><<<dim3(kNCols + 1, P.tabs ? P.ntabs : 1), 256, 0, st>>>(P);
+  narrow_merge_kernel<X4><<<dim3(P.tabs ? P.ntabs : 1, kNCols + 1), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
