@@ -664,7 +664,7 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
 // about kNarrowUnitsPerCta units each (a unit runs on one SM: large units would leave the
 // last CTAs finishing alone); units are dealt to CTAs largest first (CTA b takes units b,
 // b + grid, ...), and every unit has its own slot, merged per table in row order.
-constexpr int kNarrowUnitsPerCta = 6;
+constexpr int kNarrowUnitsPerCta = 12;
 constexpr int64_t kNarrowUnitMinStages = 64, kNarrowUnitMaxStages = 16384;
 
 struct NarrowJob {
