@@ -27,7 +27,7 @@
  * Philox4x32-10, written from its published definition (Salmon, Moraes,
  * Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3", SC'11, Sec. 4).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - randBetween(a, b) is inclusive on both ends; row i (0-based) draws
  *     (u0, u1, u2, u3) = Philox4x32-10(counter = (i_lo, i_hi, 0, 0),
  *     key = (seed_lo, seed_hi)) and maps u to a + floor(u * (b - a + 1) / 2^32).

@@ -46,7 +46,7 @@ def test_table1_identifier_and_ranges():
     for col, lo, hi in ((1, 3, 8), (2, 1, 10), (3, 1, 100)):
         vals = np.unique(iv[:, col])
         assert vals.min() == lo and vals.max() == hi and len(vals) == hi - lo + 1
-    # ranges of the derived integer columns (reading c6 of the survey; from the formulas)
+    # ranges of the derived integer columns, from the formulas
     E, F, G, H, I, K = (iv[:, j] for j in (4, 5, 6, 7, 9, 11))
     assert E.min() >= 0 and E.max() <= 209
     assert F.min() >= 0 and F.max() <= 41918
