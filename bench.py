@@ -190,6 +190,24 @@ def read_only_peak_gbs(torch, dev, gib: int = 8) -> float:
     return (gib << 30) / (best / 1e3) / 1e9
 
 
+def gemm_tflops(torch, dev, dtype, n: int) -> float:
+    """Dense GEMM rate of this GPU in `dtype` (torch.matmul, n^3, best of 3, CUDA events): the
+    measured FP64 rate that the plain FP64 comparator is set against."""
+    a = torch.randn((n, n), dtype=dtype, device=dev)
+    b = torch.randn((n, n), dtype=dtype, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -342,6 +360,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         comparator = {"kernel": "plain FP64 CUDA cores (raw moments)", "rows_per_s": n / (fp64_ms / 1e3),
                       "ms": fp64_ms, "speedup_exact_vs_fp64": fp64_ms / kernel_ms,
                       "fp64_rel_err_sumA2": relA if math.isfinite(relA) else None}
+        # its own roofline: 90 multiply-adds per row (12 sums + 78 products) against the FP64
+        # rate measured here (cuBLAS DGEMM, 4096^3, best of 3)
+        try:
+            fp64_peak = gemm_tflops(torch, dev, torch.float64, 4096)
+            achieved = 180.0 * n / (fp64_ms / 1e3) / 1e12
+            comparator.update({"fp64_tflops_achieved": achieved, "fp64_tflops_peak_measured": fp64_peak,
+                               "fp64_frac": achieved / fp64_peak})
+        except RuntimeError:
+            pass
 
     # ---- e2e: the same step through host (pinned) buffers, copies inside the timed region ----
     e2e = None
