@@ -159,10 +159,14 @@ stats_status stats_accumulate_host(stats_ctx* ctx, const void* const* hcols, int
  * small launch adds each table's per-CTA partials in a fixed order (results depend
  * only on the call, not on scheduling).  Tables whose columns sit one 16-byte-multiple
  * stride apart (a [p, ld] block) are read with 2D tensor copies, others with one bulk
- * copy per column.  Wider split tables use the tiled launch; contexts in other modes
- * go through stats_accumulate one by one.  The descriptors go to a per-device
- * workspace inside the library (grown on demand; use from one stream at a time).  A
- * context appears at most once per call.
+ * copy per column.  Exception: tables of 33..64 columns stored as such a block, with at
+ * least 4096 rows, share one persistent tcgen05 launch per mode instead (ranges of
+ * 64-row stages of any table, each range reduced into its own partial and the partials
+ * of a table added in row order).  Wider split tables use the tiled launch; contexts in
+ * other modes go through stats_accumulate one by one.  The descriptors go to per-device
+ * workspaces inside the library (grown on demand; use from one stream at a time).  A
+ * context appears at most once per call; a device-side timeout of the shared tcgen05
+ * launch is recorded in the first of its tables' contexts.
  * Errors: as stats_accumulate. */
 stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, const void* const* const* dcols,
                                       const int64_t* nrows, void* stream);

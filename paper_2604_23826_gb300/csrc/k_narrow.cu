@@ -13,7 +13,13 @@
 //           stride), and S[c][d] = D[h(c)][d] + D[l(c)][d] + D[l(d)][c] (+ sum l^2 on the
 //           diagonal).
 // TMEM lane m accumulates its own row, so each epilogue thread keeps 64 FP32 sums (BF16x4
-// adds the h and l column of each d first); the merge kernel forms S from the per-CTA slots.
+// adds the h and l column of each d first); the merge kernel forms S from the slots.
+//
+// Work comes in units: a unit is a range of 64-row stages of one table (its own tensor map,
+// pivots and tail), and CTA b takes units b, b + grid, ....  A single-table call has one
+// unit of consecutive stages per CTA; a batched call deals the units of all its 33..64-column
+// tables, largest first.  Every unit is reduced into its own slot and the merge adds a
+// table's slots in row order, so the result depends on the units only.
 //
 // In a CTA (512 threads, four warpgroups; one CTA per SM):
 //   warp 0      producer: one 3D tensor copy per 64-row stage (32 rows x 2 chunks x 64
