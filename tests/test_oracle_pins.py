@@ -321,7 +321,7 @@ def test_jacobi_reproduces_paper_table3():
                                   9.99993])).max() < 6e-5
 
 
-@pytest.mark.parametrize("p", [2, 5, 11, 40])
+@pytest.mark.parametrize("p", [2, 5, 11, 40, 129, 256])
 def test_jacobi_against_lapack(p):
     """Eigenvalues equal numpy.linalg.eigh (LAPACK); V is orthonormal; A V^T = V^T diag(ev)."""
     rng = np.random.default_rng(p)
@@ -334,3 +334,36 @@ def test_jacobi_against_lapack(p):
     assert np.abs(A @ V.T - V.T * ev).max() < 1e-10 * np.abs(ev).max()
     for k in range(p):  # sign convention: largest component positive
         assert V[k, np.argmax(np.abs(V[k]))] > 0
+
+
+def test_jacobi_repeated_eigenvalues_as_subspaces():
+    """A spectrum with a triple and a double eigenvalue (Q diag(...) Q^T, Q Haar): the
+    eigenvalues match to rounding, and the eigenvectors span the same subspaces (projectors)."""
+    rng = np.random.default_rng(21)
+    q, r = np.linalg.qr(rng.standard_normal((9, 9)))
+    q = q * np.sign(np.diag(r))
+    lam = np.array([5.0, 3.0, 3.0, 3.0, 2.0, 1.0, 1.0, 0.5, 0.25])
+    A = (q * lam) @ q.T
+    A = 0.5 * (A + A.T)
+    ev, V = O.jacobi(A)
+    assert np.allclose(ev, lam, rtol=0, atol=1e-13)
+    for lo, hi in ((1, 4), (5, 7)):
+        P = V[lo:hi].T @ V[lo:hi]
+        Pq = q[:, lo:hi] @ q[:, lo:hi].T
+        assert np.abs(P - Pq).max() < 1e-12
+    for k in (0, 4, 7, 8):  # simple eigenvalues: the vector itself, up to the sign convention
+        assert abs(abs(V[k] @ q[:, k]) - 1.0) < 1e-13
+
+
+def test_corr_from_cov_definition():
+    """corr_jk = cov_jk / sqrt(cov_jj cov_kk), unit diagonal, NaN rows and columns for a zero
+    variance (the paper's undefined correlations), on a covariance of known correlations."""
+    sd = np.array([2.0, 0.5, 3.0, 1.0])
+    R = np.array([[1.0, 0.3, -0.2, 0.0], [0.3, 1.0, 0.5, 0.1], [-0.2, 0.5, 1.0, -0.4], [0.0, 0.1, -0.4, 1.0]])
+    C = R * np.outer(sd, sd)
+    assert np.allclose(O.corr_from_cov(C), R, rtol=0, atol=1e-15)
+    C0 = C.copy()
+    C0[2, :] = C0[:, 2] = 0.0
+    K = O.corr_from_cov(C0)
+    assert np.all(np.isnan(K[2, [0, 1, 3]])) and np.all(np.isnan(K[[0, 1, 3], 2]))
+    assert K[0, 0] == 1.0 and abs(K[0, 1] - 0.3) < 1e-15
