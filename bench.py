@@ -72,6 +72,10 @@ def parse_args():
     ap.add_argument("--ntables", type=int, default=4096)
     ap.add_argument("--wave-gb", type=float, default=64.0)
     ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S")
+    ap.add_argument("--oracle-check", choices=("none", "quick", "full"), default="quick",
+                    help="tables4096: tables compared with the CPU oracle (quick: 64 of <= 1e6 rows and 16 "
+                         "larger, stratified by rows; full: every table of <= 1e6 rows and 64 larger); "
+                         "wide256: rows of the prefix compared (quick 1e6, full 1e7)")
     return ap.parse_args()
 
 
@@ -170,6 +174,34 @@ def bind_host_to_gpu(local_rank: int) -> dict:
     except Exception as e:  # no nvidia-smi or sysfs entry: leave the affinity alone
         info["error"] = type(e).__name__
     return info
+
+
+def h2d_copy_rate(torch, host, chunk_rows: int, dev, reps: int = 5) -> float:
+    """Host-to-device rate of the e2e path's own copies without the pass: the same pinned host
+    columns, one cudaMemcpyAsync per column per chunk of chunk_rows rows into two alternating
+    device staging buffers, on a side stream (as stats_accumulate_host issues them); GB/s,
+    best of `reps` passes over the whole table."""
+    n = host[0].numel()
+    stage = [[torch.empty(min(chunk_rows, n), dtype=h.dtype, device=dev) for h in host] for _ in range(2)]
+    s = torch.cuda.Stream(device=dev)
+    best = float("inf")
+    with torch.cuda.stream(s):
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            b = 0
+            for r0 in range(0, n, chunk_rows):
+                rows = min(chunk_rows, n - r0)
+                for h, d in zip(host, stage[b]):
+                    d[:rows].copy_(h[r0:r0 + rows], non_blocking=True)
+                b ^= 1
+            e1.record(s)
+            s.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    nbytes = sum(h.numel() * h.element_size() for h in host)
+    del stage
+    return nbytes / (best / 1e3) / 1e9
 
 
 def read_only_peak_gbs(torch, dev, gib: int = 8) -> float:
@@ -295,9 +327,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     gen_ms = g0.elapsed_time(g1)
 
-    cfg = G.stats_table1_config(layout, row0 + n, G.STATS_EXACT)
+    cfg = G.stats_table1_config(layout, world * n, G.STATS_EXACT)
     ctx = G.stats_init(cfg)
     pass_events = []
+    from paper_2604_23826_gb300 import shard
+    combined = {}
 
     def step(record: bool):
         G.stats_reset(ctx)
@@ -309,7 +343,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if record:
             e1.record(stream)
             pass_events.append((e0, e1))
-        return G.stats_finalize(ctx, 0)
+        if world == 1:
+            return G.stats_finalize(ctx, 0)
+        # the one exchange of the sharded pass: every rank's (n, s, S) exported, gathered in rank
+        # order, imported and merged; the analysis is of the whole table
+        merged = shard.combine_contexts(ctx)
+        try:
+            an = G.stats_finalize(merged, 0)
+            combined["raw"] = G.stats_raw(merged)
+            return an
+        finally:
+            merged.close()
 
     for _ in range(args.warmup):
         step(False)
@@ -333,12 +377,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     elapsed_ms = t0.elapsed_time(t1)
     kernel_ms = sum(a.elapsed_time(b) for a, b in pass_events) / len(pass_events)
 
-    # correctness of what was timed: identifier closed forms of this rank's rows
+    # correctness of what was timed: identifier closed forms of this rank's rows and, with
+    # several ranks, of the whole table's rows in the combined statistics
     raw = G.stats_raw(ctx)
     lo, hi = row0, row0 + n
     checks = {"sumA": raw.s_exact[0] == hi * (hi + 1) // 2 - lo * (lo + 1) // 2,
               "sumA2": raw.S_exact[0][0] == (hi * (hi + 1) * (2 * hi + 1) - lo * (lo + 1) * (2 * lo + 1)) // 6,
               "n": raw.n == n}
+    if world > 1:
+        g, N = combined["raw"], world * n
+        checks["combined_n"] = g.n == N
+        checks["combined_sumA"] = g.s_exact[0] == N * (N + 1) // 2
+        checks["combined_sumA2"] = g.S_exact[0][0] == N * (N + 1) * (2 * N + 1) // 6
 
     # ---- the plain FP64 comparator on the same table (the metric's "vs plain FP64") ----
     comparator = None
@@ -396,7 +446,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
-            k_e2e = max(2, min(args.steps, 4))
+            k_e2e = max(3, min(args.steps, 10))
             h0 = torch.cuda.Event(enable_timing=True)
             h1 = torch.cuda.Event(enable_timing=True)
             h0.record(stream)
@@ -405,25 +455,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             h1.record(stream)
             torch.cuda.synchronize()
             e2e_ms = h0.elapsed_time(h1) / k_e2e
-            # the link's own rate: one pinned 4 GiB host -> device copy (the e2e path's roofline)
-            probe_h = host[0].view(torch.uint8)[: min(host[0].numel() * host[0].element_size(), 1 << 32)]
-            probe_d = torch.empty_like(probe_h, device=dev)
-            probe_d.copy_(probe_h, non_blocking=True)
-            torch.cuda.synchronize()
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            probe_d.copy_(probe_h, non_blocking=True)
-            c1.record(stream)
-            torch.cuda.synchronize()
-            h2d_gbs = probe_h.numel() / (c0.elapsed_time(c1) / 1e3) / 1e9
-            del probe_d
+            # the e2e path's roofline: its own copies (same buffers, chunks and copy calls) alone
+            h2d_gbs = h2d_copy_rate(torch, host, args.chunk_rows, dev)
             pa = 11
             T = 12 * 13 // 2
             result_bytes = 8 * (1 + 12 + T + 2 * 12 + 2 * T + pa + 3 * pa * pa + pa + 8) + 8 + 4
             e2e = {"value": n_e2e / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": n_e2e * bpr,
                    "d2h_bytes_per_step": result_bytes, "rows": n_e2e, "ms_per_step": e2e_ms, "steps": k_e2e,
                    "h2d_GBps_achieved": n_e2e * bpr / (e2e_ms / 1e3) / 1e9, "h2d_GBps_measured_copy": h2d_gbs,
+                   "h2d_copy_probe": "the same pinned columns copied chunk by chunk (one cudaMemcpyAsync per "
+                                     "column per chunk, two staging buffers) with no pass, best of 5",
                    "h2d_frac": (n_e2e * bpr / (e2e_ms / 1e3) / 1e9) / h2d_gbs,
                    "api": "stats_accumulate_host (pinned host columns, double-buffered chunks) + stats_finalize",
                    "host_affinity": {k: v for k, v in affinity.items() if not k.startswith("_")}}
@@ -476,7 +517,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": f"table1_n{n:.0e}_seed{SEED}_{args.layout}".replace("+", ""), "rows_per_gpu": n,
                    "p": 12, "layout": args.layout, "bytes_per_row": bpr, "mode": "STATS_EXACT",
                    "step": "exact fused pass + finalize (mean, cov, corr, PCA) + D2H of the result",
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"rows sharded, {world} replica(s)"},
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"rows sharded over {world} rank(s)" + (
+                       "; each step ends with the export / rank-ordered gather / import + merge of the ranks' "
+                       "statistics, then the analysis of the whole table" if world > 1 else "")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "traffic": traffic,
                      "kernel": "exact_pass_kernel<ConvT1>", "kernel_ms": kernel_ms,
@@ -486,7 +530,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                      "frac_read_only": achieved / read_peak if read_peak else None},
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "gpu_launches": 2 * args.steps,
+        # per step: the pass and finalize, plus one merge launch per other rank's image
+        "gpu_launches": (2 + (world - 1)) * args.steps,
         "clocks": clocks,
         "generator": {"rows_per_s": n / (gen_ms / 1e3), "GB_per_s_written": n * bpr / (gen_ms / 1e3) / 1e9},
         "comparator": comparator,
@@ -595,6 +640,38 @@ def run_tables(args, rank: int, world: int, local_rank: int):
         n, p, mu, sd = params[t]
         mu32, sd32 = np.float32(mu).astype(np.float64), np.float32(sd).astype(np.float64)
         worst_mean_rel = max(worst_mean_rel, float(np.max(np.abs(an.mean - mu32) / sd32)) * math.sqrt(n))
+    oracle_check = None
+    if args.oracle_check != "none" and rank == 0:
+        # the same tables regenerated (same seeds, same values), copied back, and the oracle's
+        # two-pass covariance compared with the batched pass's result
+        import oracle as O
+        spec = {"quick": dict(n_small=64, n_large=16), "full": dict(n_small=None, n_large=64)}[args.oracle_check]
+        pick = set(inputs.check_sample([params[t] for t in mine], **spec))
+        pick = {mine[i] for i in pick}
+        fin_of = dict(zip(mine, finals))
+        worst, worst_t, o_secs = 0.0, None, 0.0
+        for g in groups:
+            if not pick.intersection(g):
+                continue
+            views = materialise(g)
+            for t, v in zip(g, views):
+                if t not in pick:
+                    continue
+                H = v.cpu().numpy()
+                o0 = time.perf_counter()
+                cov = O.cov_twopass_columns([H[j].astype(np.float64) for j in range(H.shape[0])])
+                o_secs += time.perf_counter() - o0
+                err = float(np.linalg.norm(fin_of[t].cov - cov) / np.linalg.norm(cov))
+                if err >= worst:
+                    worst, worst_t = err, t
+        oracle_check = {"cov_rel_vs_oracle": worst, "tables": len(pick),
+                        "rows": int(sum(params[t][0] for t in pick)),
+                        "worst_table": {"index": worst_t, "n": params[worst_t][0], "p": params[worst_t][1]},
+                        "sample": args.oracle_check + ": " + ("64 tables of <= 1e6 rows and 16 larger, stratified"
+                                                             " by rows" if args.oracle_check == "quick" else
+                                                             "every table of <= 1e6 rows and 64 larger, "
+                                                             "stratified by rows"),
+                        "oracle_s": o_secs, "tolerance": 2e-6}
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs") or 6800.0
     achieved = bytes_total / (ms / 1e3) / 1e9
@@ -618,7 +695,8 @@ def run_tables(args, rank: int, world: int, local_rank: int):
             "kernel_ms": ms, "algorithmic_bytes": bytes_total}
     extra = {"finalize_ms_all_tables_batched": fin_ms,
              "host_ms_per_call": sum(host_ms) / max(1, len(host_ms)),
-             "check_means_within_sqrt_n_sigma_units": worst_mean_rel}
+             "check_means_within_sqrt_n_sigma_units": worst_mean_rel,
+             "oracle_check": oracle_check}
     out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, batched FP32 tables",
                      rows_all / (ms_all / 1e3), ms_all, config, roof, clocks,
                      launches_per_step * args.steps, extra)
@@ -694,6 +772,24 @@ def run_wide(args, rank: int, world: int, local_rank: int):
                           "snapshot_seeded_ms": snap_ms, "snapshot_seeded_sweeps": an2.sweeps,
                           "cov": an.cov}
     clocks = sampler.stop()
+    if args.oracle_check != "none" and rank == 0:
+        # the oracle on a prefix of the same table, against each mode's pass over that prefix
+        import oracle as O
+        m = min(n, 1_000_000 if args.oracle_check == "quick" else 10_000_000)
+        H = X[:, :m].cpu().numpy()
+        o0 = time.perf_counter()
+        cov_o = O.cov_twopass_columns([H[j].astype(np.float64) for j in range(p)])
+        o_secs = time.perf_counter() - o0
+        del H
+        ev_o = np.linalg.eigvalsh(cov_o)[::-1][:10]
+        for mname in modes:
+            with G.stats_init(G.Config([G.STATS_F32] * p, getattr(G, MODE_NAMES[mname]), [0] * p)) as ctx:
+                G.stats_accumulate(ctx, [c[:m] for c in cols], m, stream)
+                an_m = G.stats_finalize(ctx, 0)
+            results[mname]["oracle_check"] = {
+                "rows": m, "cov_rel_vs_oracle": float(np.linalg.norm(an_m.cov - cov_o) / np.linalg.norm(cov_o)),
+                "top10_eval_rel_vs_oracle": float(np.max(np.abs(an_m.evals[:10] - ev_o) / ev_o)),
+                "oracle_s": o_secs, "sample": f"the table's first {m} rows on both sides"}
     ref = results.get("FP64S")
     main_mode = modes[0]
     for mname, r in results.items():

@@ -78,6 +78,10 @@ typedef enum { STATS_I16 = 0, STATS_I32 = 1, STATS_I64 = 2, STATS_F32 = 3, STATS
  *                      on tensor cores (each 16-row block a fresh FP32 chain, added in
  *                      round-to-nearest FP32, then double-double); for p <= 64 plus the
  *                      diagonal of L^T L from the CUDA cores (its missing positive bias).
+ *                      While a ctx holds fewer than 64 p rows (this call's included) its
+ *                      calls form all four products, as STATS_BF16X4 does: the off-diagonal
+ *                      L^T L terms that BF16X3 drops cancel only as 1/sqrt(n) and would leave
+ *                      about 2.6e-6 sqrt(p / n) of relative error at small n.
  *   STATS_BF16X4       as BF16X3 plus all of L^T L on the tensor cores.
  *   STATS_FP32         FP32 CUDA-core FMA on x - c, flushed into FP32 (hi, lo) pairs.
  * The BF16 modes take FP32 columns only; the others take any dtype.             */
@@ -276,6 +280,20 @@ int32_t stats_num_analysis_columns(const stats_ctx* ctx);
  * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
 
+/* Testing knob of the bounded grid-wide waits of the eigen-solver that stats_finalize and
+ * stats_finalize_warm run over the whole GPU (more than 23 analysis columns, or a seed).
+ *   wait_ns       how long a block waits at a grid barrier before the call gives up with
+ *                 STATS_ETIMEOUT (0 = the default 2 s; at most 60 s)
+ *   absent_block  -1 (normal), or the index of a block of the eigen-solver's grid that leaves
+ *                 before its first arrival: every other block's wait at that barrier then
+ *                 runs out after wait_ns, the eigenpairs are not written, and the call
+ *                 returns STATS_ETIMEOUT.  This exercises the stalled-block failure path
+ *                 (the error word, every block leaving, the host reading the status) with no
+ *                 device fault; the ctx stays usable.  A block index past the grid has no
+ *                 effect.
+ * Applies to later finalize calls on ctx.  Errors: EINVAL. */
+stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent_block);
+
 /* Tuning knob of STATS_BF16X3 / STATS_BF16X4 (16..4096, a multiple of 16): rows of
  * round-to-nearest FP32 accumulation of a warp before its (hi, lo) pairs (default
  * 1024 for p > 64, 16384 for p <= 64).  Every 16-row block is a fresh tensor-core
@@ -322,10 +340,10 @@ int32_t stats_table1_row_bytes(int32_t layout);
 
 /* ---------------------------------------------------------------------------
  * No-allocation variant of the exact pass.  The paper has no counterpart: this
- * entry point exists for callers that cannot allocate device memory -- code
- * running while a stream is captured into a CUDA graph under the global capture
- * mode, where cudaMalloc is not allowed, or an application that keeps a fixed
- * device budget and lets no library allocate outside it.
+ * entry point exists for callers that cannot allocate device memory -- a serving
+ * process or framework that reserves the GPU's memory up front in its own pool
+ * and lets no library call cudaMalloc outside it, or code that must not block
+ * the device (cudaFree synchronises it).
  *
  * It computes (n, s, S) of nrows rows (dcols: host array of cfg->p device
  * pointers, as for stats_accumulate) with the exact pass and writes them to the
@@ -348,7 +366,9 @@ int32_t stats_table1_row_bytes(int32_t layout);
  * on every GPU that loads the library until the process exits.  No cudaMalloc,
  * cudaFree or allocating library routine is called.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) once; make that
- * first call before any stream capture begins.  All calls share the one array:
+ * first call before any stream capture begins.  The address stays valid until the
+ * device is reset (cudaDeviceReset), which invalidates it together with every
+ * other context and pointer of this library on that device.  All calls share the one array:
  * each call clears it first, and calls whose work overlaps on the GPU (for
  * example on two streams) race on it and must be serialised by the caller.
  * Asynchronous on stream; results are valid once the stream reaches them.

@@ -295,6 +295,15 @@ def stats_set_flush_rows(ctx: Ctx, rows: int):
     _check(L.stats_set_flush_rows(ctx.handle, rows), "stats_set_flush_rows")
 
 
+def stats_set_grid_wait(ctx: Ctx, wait_ns: int = 0, absent_block: int = -1):
+    """Limit of the eigen-solver's bounded grid-wide waits (0: 2 s), and optionally a block that
+    leaves before arriving, so that the other blocks' waits run out (stats.h)."""
+    L = load()
+    L.stats_set_grid_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]
+    L.stats_set_grid_wait.restype = ctypes.c_int
+    _check(L.stats_set_grid_wait(ctx.handle, wait_ns, absent_block), "stats_set_grid_wait")
+
+
 def stats_num_analysis_columns(ctx: Ctx) -> int:
     return load().stats_num_analysis_columns(ctx.handle)
 
@@ -474,6 +483,23 @@ def gen_table1(seed: int, nrows: int, layout: int = STATS_T1_L32, row0: int = 0,
     return cols
 
 
+# ----------------------------------------------------------------------------- record checks
+def identifier_checks(raw: Raw, first: int, count: int, col: int = 0) -> dict:
+    """Closed-form checks that every record of a row range was processed exactly once.
+
+    The paper validates its pipeline by the identifier column's sum ("Validation and
+    Infrastructure Testing"): a column holding first, first + 1, ..., first + count - 1
+    (Table 1's A is the 1-based row index) must give n = count, its sum
+    count (first + last) / 2 and its sum of squares sum_{v <= last} v^2 - sum_{v < first} v^2,
+    with v^2 sums k (k + 1) (2k + 1) / 6.  A dropped, repeated or displaced chunk changes at
+    least one of them.  raw must hold exact sums (STATS_EXACT, integer identifier column)."""
+    last = first + count - 1
+    sq = lambda k: k * (k + 1) * (2 * k + 1) // 6  # noqa: E731
+    return {"n": raw.n == count,
+            "sum": raw.s_exact[col] == count * (first + last) // 2,
+            "sum_sq": raw.S_exact[col][col] == sq(last) - sq(first - 1)}
+
+
 # ----------------------------------------------------------------------------- no-allocation variant
 def noalloc_result_bytes(p: int) -> int:
     """STATS_NOALLOC_RESULT_BYTES(p) of stats.h."""
@@ -518,7 +544,8 @@ def parse_noalloc_result(buf: bytes, p: int) -> Raw:
             S[j, k] = S[k, j] = Su[t]
             SE[j][k] = SE[k][j] = S_ex_u[t]
             t += 1
-    code = STATS_ERANGE if status & 1 else STATS_ETIMEOUT if status & 2 else \
+    # the order of the regular entry points: an expired wait first, then a range error
+    code = STATS_ETIMEOUT if status & 2 else STATS_ERANGE if status & 1 else \
         STATS_EOVERFLOW if d[flags] != 0.0 else STATS_OK
     return Raw(n, s, S, s_ex, SE, code)
 

@@ -89,6 +89,8 @@ struct stats_ctx {
   unsigned int* d_split_ticket = nullptr;
   int split_grid = 0;
   int flush_rows = 0;                   // 0: by table width
+  int64_t grid_wait_ns = 0;             // eigen-solver grid waits: limit (0: 2 s)
+  int32_t grid_absent_block = -1;       // testing: a block of the eigen-solver that never arrives
   // the last 2D tensor map made for this ctx's FP32 columns (reused while the layout is the same)
   const void* tmap_base = nullptr;
   int64_t tmap_stride = 0, tmap_rows = 0;
@@ -117,6 +119,8 @@ struct stats_ctx {
   cudaStream_t last = nullptr;
   int grid = 0;
   int sms = 0;
+  // rows enqueued into the accumulator so far (host-side count; reset, merge and import keep it)
+  int64_t rows_enqueued = 0;
   stats_status sticky = STATS_OK;
 };
 
@@ -183,81 +187,109 @@ bool real_field(bool bounded, double lo, double hi, ColPlan& cp) {
   return true;
 }
 
-bool is_t1_plan(const stats_ctx* c, int layout) {
-  if (c->p != 12) return false;
+// Whether a column plan is one of the Table 1 layouts that the specialised converters read
+// (the dtypes of the layout, and digit fields no wider than the converter handles).
+bool is_t1_plan(int p, const int32_t* dtypes, const ColPlan* cp, int layout) {
+  if (p != 12) return false;
   static const int32_t l32[12] = {I64, I32, I32, I32, I32, I32, I32, I32, F64, I32, F64, I32};
   static const int32_t l16[12] = {I64, I16, I16, I16, I16, I32, I16, I16, F64, I16, F64, I16};
   const int32_t* want = layout ? l16 : l32;
   for (int j = 0; j < 12; ++j)
-    if (c->dtypes[j] != want[j]) return false;
-  const auto& P = c->plan;
+    if (dtypes[j] != want[j]) return false;
   for (int j : {1, 2, 3, 4, 6, 7, 11})
-    if (P[j].is_signed || P[j].k != 1) return false;
+    if (cp[j].is_signed || cp[j].k != 1) return false;
   for (int j : {5, 9})
-    if (P[j].is_signed || P[j].k > 2) return false;
-  if (P[0].is_signed || P[0].k > 5) return false;
-  if (!P[8].is_real || !P[8].is_signed) return false;
-  if (!P[10].is_real || P[10].is_signed) return false;
+    if (cp[j].is_signed || cp[j].k > 2) return false;
+  if (cp[0].is_signed || cp[0].k > 5) return false;
+  if (!cp[8].is_real || !cp[8].is_signed) return false;
+  if (!cp[10].is_real || cp[10].is_signed) return false;
   return true;
 }
 
-void set_t1_offsets(stats_ctx* c) {
-  // slots: 0 ones | 1 B | 2 C | 3 D | 4 E | 5 G | 6 H | 7 K | 8-9 F | 10-11 I | 12-16 A | 17-23 cotC | 24-30 J
-  static const int off[12] = {12, 1, 2, 3, 4, 8, 5, 6, 17, 10, 24, 7};
-  static const int k[12] = {5, 1, 1, 1, 1, 2, 1, 1, 7, 2, 7, 1};
-  for (int j = 0; j < 12; ++j) {
-    c->plan[j].off = off[j];
-    c->plan[j].k = k[j];
+// The digit plan of STATS_EXACT for a configuration, in fixed-size arrays (no heap use), for
+// stats_init and the no-allocation entry point alike: each column's digit field (bytes, sign,
+// real scaling) and first digit slot; the converter (a Table 1 layout, whose slots are fixed,
+// or the generic one with its table of digit pairs); and the pipeline's stage layout.
+stats_status exact_plan(int p, const int32_t* dtypes, bool bounded, const double* lo, const double* hi,
+                        ColPlan (&cp)[kMaxCols], ExactParams& xp, int& conv) {
+  if (p < 1 || p > kMaxCols || !dtypes || (bounded && (!lo || !hi))) return STATS_EINVAL;
+  for (int j = 0; j < p; ++j) {
+    const int32_t dt = dtypes[j];
+    if (dt < I16 || dt > F64) return STATS_EINVAL;
+    cp[j] = ColPlan{};
+    const double l = bounded ? lo[j] : 0.0, h = bounded ? hi[j] : 0.0;
+    const bool ok = (dt == F32 || dt == F64) ? real_field(bounded, l, h, cp[j]) : int_field(dt, bounded, l, h, cp[j]);
+    if (!ok) return STATS_EINVAL;
   }
+  conv = CONV_GENERIC;
+  for (int layout = 0; layout < 2; ++layout)
+    if (is_t1_plan(p, dtypes, cp, layout)) {
+      conv = layout ? CONV_T1_L16 : CONV_T1_L32;
+      // slots: 0 ones | 1 B | 2 C | 3 D | 4 E | 5 G | 6 H | 7 K | 8-9 F | 10-11 I | 12-16 A | 17-23 cotC | 24-30 J
+      static const int off[12] = {12, 1, 2, 3, 4, 8, 5, 6, 17, 10, 24, 7};
+      static const int k[12] = {5, 1, 1, 1, 1, 2, 1, 1, 7, 2, 7, 1};
+      for (int j = 0; j < 12; ++j) {
+        cp[j].off = off[j];
+        cp[j].k = k[j];
+      }
+      break;
+    }
+  if (conv == CONV_GENERIC) {
+    int slot = 1;
+    for (int j = 0; j < p; ++j) {
+      cp[j].off = slot;
+      slot += cp[j].k;
+    }
+    if (slot > kDigits) return STATS_EINVAL;
+    // per digit slot: source column (-1 the ones column, -2 padding), byte, signed top byte
+    int8_t col[kDigits], byt[kDigits], sg[kDigits];
+    for (int q = 0; q < kDigits; ++q) {
+      col[q] = -2;
+      byt[q] = 0;
+      sg[q] = 0;
+    }
+    col[0] = -1;
+    for (int j = 0; j < p; ++j)
+      for (int a = 0; a < cp[j].k; ++a) {
+        col[cp[j].off + a] = static_cast<int8_t>(j);
+        byt[cp[j].off + a] = static_cast<int8_t>(a);
+        sg[cp[j].off + a] = (cp[j].is_signed && a == cp[j].k - 1) ? 1 : 0;
+      }
+    for (int q = 0; q < kDigitPairs; ++q) {
+      xp.pc0[q] = col[2 * q];
+      xp.pb0[q] = byt[2 * q];
+      xp.ps0[q] = sg[2 * q];
+      xp.pc1[q] = col[2 * q + 1];
+      xp.pb1[q] = byt[2 * q + 1];
+      xp.ps1[q] = sg[2 * q + 1];
+    }
+  }
+  int off = 0;
+  for (int j = 0; j < p; ++j) {
+    const int b = dtype_bytes(dtypes[j]);
+    xp.dtype[j] = dtypes[j];
+    xp.col_bytes[j] = b;
+    xp.col_off[j] = off;
+    off += stage_col_bytes(b);
+    xp.real_shift[j] = cp[j].shift;
+    xp.real_emax[j] = cp[j].emax;
+    xp.kbytes[j] = cp[j].k;
+    xp.is_signed[j] = cp[j].is_signed;
+  }
+  xp.p = p;
+  xp.stage_bytes = off;
+  xp.stages = exact_pick_stages(off);
+  if (xp.stages == 0) return STATS_EINVAL;  // rows too wide for the pipeline
+  return STATS_OK;
 }
 
 stats_status build_plan(stats_ctx* c) {
-  c->plan.assign(c->p, ColPlan{});
-  for (int j = 0; j < c->p; ++j) {
-    const int32_t dt = c->dtypes[j];
-    ColPlan& cp = c->plan[j];
-    if (dt == F32 || dt == F64) {
-      if (!real_field(c->has_bounds, c->has_bounds ? c->lo[j] : 0, c->has_bounds ? c->hi[j] : 0, cp))
-        return STATS_EINVAL;
-    } else if (!int_field(dt, c->has_bounds, c->has_bounds ? c->lo[j] : 0, c->has_bounds ? c->hi[j] : 0, cp)) {
-      return STATS_EINVAL;
-    }
-  }
-  if (is_t1_plan(c, 0) || is_t1_plan(c, 1)) {
-    c->conv = is_t1_plan(c, 0) ? CONV_T1_L32 : CONV_T1_L16;
-    set_t1_offsets(c);
-    return STATS_OK;
-  }
-  if (c->p > kMaxCols) return STATS_EINVAL;
-  int slot = 1;
-  for (int j = 0; j < c->p; ++j) {
-    c->plan[j].off = slot;
-    slot += c->plan[j].k;
-  }
-  if (slot > kDigits) return STATS_EINVAL;
-  c->conv = CONV_GENERIC;
-  // generic pair plan
-  int8_t col[kDigits], byt[kDigits], sg[kDigits];
-  for (int s = 0; s < kDigits; ++s) {
-    col[s] = -2;
-    byt[s] = 0;
-    sg[s] = 0;
-  }
-  col[0] = -1;
-  for (int j = 0; j < c->p; ++j)
-    for (int a = 0; a < c->plan[j].k; ++a) {
-      col[c->plan[j].off + a] = static_cast<int8_t>(j);
-      byt[c->plan[j].off + a] = static_cast<int8_t>(a);
-      sg[c->plan[j].off + a] = (c->plan[j].is_signed && a == c->plan[j].k - 1) ? 1 : 0;
-    }
-  for (int q = 0; q < kDigitPairs; ++q) {
-    c->xp.pc0[q] = col[2 * q];
-    c->xp.pb0[q] = byt[2 * q];
-    c->xp.ps0[q] = sg[2 * q];
-    c->xp.pc1[q] = col[2 * q + 1];
-    c->xp.pb1[q] = byt[2 * q + 1];
-    c->xp.ps1[q] = sg[2 * q + 1];
-  }
+  ColPlan cp[kMaxCols];
+  const stats_status s = exact_plan(c->p, c->dtypes.data(), c->has_bounds, c->lo.data(), c->hi.data(), cp, c->xp,
+                                    c->conv);
+  if (s != STATS_OK) return s;
+  c->plan.assign(cp, cp + c->p);
+  c->stages = c->xp.stages;
   return STATS_OK;
 }
 
@@ -296,6 +328,20 @@ stats_status ensure_slots(stats_ctx* c, int grid) {
   return STATS_OK;
 }
 
+// BF16x3 drops the off-diagonal products of the low halves, sum_i l_ij l_ik.  Their sum
+// over n rows is a sum of products of rounding residuals (|l| <= 2^-9 |x - c|) with random
+// signs: it grows as sqrt(n) while the covariance grows as n, so the relative Frobenius
+// error it leaves is about 2.6e-6 * sqrt(p / n) for independent columns.  Until a context
+// holds 64 p rows (error ~3e-7 there) its calls form all four products, as BF16x4 does;
+// from then on the rows taken with three products are at least as many as would bring
+// their own share of the error below that level.
+constexpr int64_t kBf16x3RowsPerColumn = 64;
+
+bool split_x4(const stats_ctx* c, int64_t nrows) {
+  if (c->mode == STATS_BF16X4) return true;
+  return c->mode == STATS_BF16X3 && c->rows_enqueued + nrows < kBf16x3RowsPerColumn * c->p;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 tables of up to 64 columns in BF16x3 / BF16x4 mode: register-fragment
 // tensor-core pass over a list of (table, row range) units.  The launch's
@@ -306,6 +352,7 @@ struct Gram32Job {
   stats_ctx* c;
   const void* const* cols;
   int64_t nrows;
+  bool x4;  // all four products (BF16x4, or a BF16x3 context still below its row threshold)
 };
 
 struct Gram32Workspace {
@@ -396,7 +443,7 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
     for (int x4 = 0; x4 < 2; ++x4) {
       std::vector<const Gram32Job*> all;
       for (const Gram32Job& j : jobs)
-        if (gram32_width(j.c->p) == P && (j.c->mode == STATS_BF16X4) == (x4 == 1) && j.nrows > 0) all.push_back(&j);
+        if (gram32_width(j.c->p) == P && j.x4 == (x4 == 1) && j.nrows > 0) all.push_back(&j);
       for (size_t first = 0; first < all.size(); first += kGram32MaxTables) {
         const size_t nt = std::min<size_t>(kGram32MaxTables, all.size() - first);
         const int64_t rs = gram32_rows_per_stage(P);
@@ -575,7 +622,8 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
     c->shift_set = true;
   }
   WideParams W{};
-  const int grid = wide_plan(c->p, c->sms, c->mode == STATS_BF16X4, W);
+  const bool x4 = split_x4(c, nrows);
+  const int grid = wide_plan(c->p, c->sms, x4, W);
   if (grid <= 0) return STATS_EINVAL;
   if (!c->d_wide_slots || c->wide_grid_alloc < grid) {
     if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
@@ -602,7 +650,7 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
   W.p = c->p;
   const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
   W.flush_chains = std::max(1, flush_rows / wide_chunk_rows());
-  CK(c, launch_wide(W, c->mode == STATS_BF16X4, grid, st));
+  CK(c, launch_wide(W, x4, grid, st));
   return STATS_OK;
 }
 
@@ -655,7 +703,7 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
   P.slots = c->d_wide_slots;
   P.status = c->d_status;
   P.flush_stages = narrow_flush_stages(c);
-  CK(c, launch_narrow(P, c->mode == STATS_BF16X4, grid, st));
+  CK(c, launch_narrow(P, split_x4(c, nrows), grid, st));
   return STATS_OK;
 }
 
@@ -785,7 +833,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     stats_status s = run_narrow(c, dcols, nrows, st);
     if (s != STATS_OK) return s;
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64) {
-    std::vector<Gram32Job> jobs{{c, dcols, nrows}};
+    std::vector<Gram32Job> jobs{{c, dcols, nrows, split_x4(c, nrows)}};
     stats_status s = run_gram32(jobs, st);
     if (s != STATS_OK) return s;
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && wide_eligible(c, dcols, nrows)) {
@@ -827,7 +875,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     S.acc_S = c->d_fS;
     S.acc_S_lo = c->d_fS_lo;
     S.acc_n = c->d_fn;
-    CK(c, launch_split(S, T, c->mode == STATS_BF16X4, g, st));
+    CK(c, launch_split(S, T, split_x4(c, nrows), g, st));
   } else if (c->mode == STATS_FP32 || c->p > 12) {
     // tiled CUDA-core pass: FP32-core, or FP64 for tables wider than the row kernel
     CoreParams C{};
@@ -893,6 +941,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     P.acc_n = c->d_fn;
     CK(c, launch_fp64(P, grid, st));
   }
+  c->rows_enqueued += nrows;
   c->last = st;
   return STATS_OK;
 }
@@ -959,6 +1008,8 @@ stats_status run_finalize(stats_ctx* c, int want_pca, int pca_on, const double* 
     J.flags_off = c->lay.flags;
     J.pa = pa;
     J.m = static_cast<int32_t>(m);
+    J.wait_ns = c->grid_wait_ns;
+    J.absent_block = c->grid_absent_block;
     F.defer_A = J.a;
     F.defer_ctl = const_cast<int32_t*>(J.ctl);
     F.defer_m = J.m;
@@ -1038,35 +1089,11 @@ stats_status create(stats_ctx** out, const stats_config* cfg) {
 
   stats_status s = STATS_OK;
   if (c->mode == STATS_EXACT) {
-    s = build_plan(c);
+    s = build_plan(c);  // digit plan, converter and stage layout
     if (s != STATS_OK) {
       delete c;
       return s;
     }
-    // pipeline stage layout
-    int off = 0;
-    int row_bytes = 0;
-    for (int j = 0; j < c->p; ++j) {
-      const int b = dtype_bytes(c->dtypes[j]);
-      c->xp.dtype[j] = c->dtypes[j];
-      c->xp.col_bytes[j] = b;
-      c->xp.col_off[j] = off;
-      off += stage_col_bytes(b);
-      row_bytes += b;
-      c->xp.real_shift[j] = c->plan[j].shift;
-      c->xp.real_emax[j] = c->plan[j].emax;
-      c->xp.kbytes[j] = c->plan[j].k;
-      c->xp.is_signed[j] = c->plan[j].is_signed;
-    }
-    c->xp.p = c->p;
-    c->xp.stage_bytes = off;
-    c->stages = exact_pick_stages(off);
-    if (c->stages == 0) {
-      delete c;
-      return STATS_EINVAL;  // rows too wide for the pipeline
-    }
-    c->xp.stages = c->stages;
-    (void)row_bytes;
   }
   // device allocations
   cudaError_t e = cudaSuccess;
@@ -1496,10 +1523,13 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
       for (int j = 0; j < c->p; ++j)
         if (!dcols[t][j] || (reinterpret_cast<uintptr_t>(dcols[t][j]) & 3u)) return STATS_EINVAL;
+      const bool x4 = split_x4(c, nrows[t]);
       if (c->p > 32 && c->p <= 64 && nrows[t] >= kNarrowBatchMinRows && narrow_eligible(c, dcols[t], nrows[t])) {
-        narrow[c->mode == STATS_BF16X4 ? 1 : 0].push_back({c, dcols[t], nrows[t]});
+        narrow[x4 ? 1 : 0].push_back({c, dcols[t], nrows[t]});
+        c->rows_enqueued += nrows[t];
       } else if (c->p <= 64) {
-        g32.push_back({c, dcols[t], nrows[t]});
+        g32.push_back({c, dcols[t], nrows[t], x4});
+        c->rows_enqueued += nrows[t];
       } else if (wide_eligible(c, dcols[t], nrows[t])) {
         s = launch_pass(c, dcols[t], nrows[t], st);  // one tcgen05 launch per wide table
         if (s != STATS_OK) return s;
@@ -1572,7 +1602,8 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
     if (!c->shift_set) need_shift.push_back(static_cast<int>(i));
     for (int j = 0; j < c->p; ++j) colptrs[cp + j] = static_cast<const float*>(dcols[t][j]);
     cp += c->p;
-    const int a = T == 64 ? 1 : 0, b = c->mode == STATS_BF16X4 ? 1 : 0;
+    const int a = T == 64 ? 1 : 0, b = split_x4(c, nrows[t]) ? 1 : 0;
+    c->rows_enqueued += nrows[t];
     for (int u = 0; u < g; ++u) {
       units[a][b].push_back(make_int2(static_cast<int>(i), u));
       unit_rows[a][b].push_back(nrows[t] / S.ksplit);
@@ -1659,6 +1690,7 @@ stats_status stats_merge(stats_ctx* dst, const stats_ctx* src) {
     CK(dst, cudaMemcpy(dst->d_status, &mine, sizeof(mine), cudaMemcpyHostToDevice));
   }
   cudaStream_t st = dst->last;
+  dst->rows_enqueued += src->rows_enqueued;
   if (shifted && !src->shift_set) return STATS_OK;  // src holds no rows
   if (shifted && dst->shift_set) {
     // the two ctxs generally have different pivots: re-express src about dst's pivot
@@ -1705,6 +1737,7 @@ stats_status stats_reset(stats_ctx* ctx) {
     ctx->shift_set = false;
   }
   CK(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), st));
+  ctx->rows_enqueued = 0;
   return STATS_OK;
 }
 
@@ -1897,6 +1930,7 @@ stats_status stats_import(stats_ctx** out, const void* buf, size_t len) {
     stats_destroy(c);
     return STATS_ECUDA;
   }
+  if (mode != STATS_EXACT) memcpy(&c->rows_enqueued, r + (2 * p + 2 * T + p) * sizeof(double), sizeof(int64_t));
   c->shift_set = ss != 0;
   if (c->shift_set && c->d_fshift) {  // the split kernels' float copy of the pivot
     e = launch_pivot_to_float(c->d_shift, c->d_fshift, p, nullptr);
@@ -1935,6 +1969,13 @@ const char* stats_strerror(stats_status st) {
 }
 
 int32_t stats_num_analysis_columns(const stats_ctx* ctx) { return ctx ? ctx->pa : -1; }
+
+stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent_block) {
+  if (!ctx || wait_ns < 0 || wait_ns > int64_t(60) * 1000000000 || absent_block < -1) return STATS_EINVAL;
+  ctx->grid_wait_ns = wait_ns;
+  ctx->grid_absent_block = absent_block;
+  return STATS_OK;
+}
 
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks) {
   if (!ctx || blocks < 0) return STATS_EINVAL;
@@ -1986,21 +2027,23 @@ stats_status stats_gen_table1(uint64_t seed, uint64_t row0, int64_t nrows, int32
 // ---------------------------------------------------------------------------
 // The no-allocation entry point.
 //
-// Some callers cannot allocate device memory: code that runs while a stream is
-// being captured into a CUDA graph under the global capture mode (where
-// cudaMalloc is not permitted), or a host application that owns a fixed device
-// memory budget and forbids any library from allocating outside it.  For them
-// stats_pass_noalloc runs the exact pass and the recombination of (n, s, S)
-// without a context: its scratch -- the digit Gram of one call, the per-call
-// staging accumulator and the ticket / error / status words -- lives in the
-// file-scope device array below (16,640 bytes, held by every GPU that loads the
-// library until the process exits).  The caller still passes the inputs and
-// the result buffer.
+// Some callers cannot allocate device memory.  A serving process or framework that
+// takes the GPU's memory up front into its own pool forbids libraries to call
+// cudaMalloc behind its back (an allocation outside the pool can fail, or steal
+// memory the pool has promised elsewhere); code that must not block, such as a
+// latency-critical loop, cannot afford cudaMalloc / cudaFree either, since
+// cudaFree synchronises the device.  Such callers can still run the exact pass
+// through stats_pass_noalloc: it takes no context, and its scratch -- the digit
+// Gram of one call, the per-call staging accumulator and the ticket / error /
+// status words -- lives in the file-scope device array below (16,640 bytes, held
+// by every GPU that loads the library until the process exits).  The caller
+// passes the inputs and the result buffer.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kNoallocWords = 2 * kDigits * kDigits + 32;  // 16,640 bytes
-constexpr int64_t kNoallocMaxRows = int64_t(1) << 46;      // digit sums stay far below 2^63
+// A digit pair sums at most 2^46 products of two digits below 256: 2^46 * 255^2 < 2^62
+constexpr int64_t kNoallocMaxRows = int64_t(1) << 46;
 
 __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
 
@@ -2008,7 +2051,9 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[64] = {};
 
 // Device address of the scratch array on the current device, looked up once per
-// device (a host-side reference to the array is not a device address).
+// device (a host-side reference to the array is not a device address).  The address
+// belongs to the device's primary context: after cudaDeviceReset it is stale, as are
+// every context and device pointer of this library on that device.
 cudaError_t noalloc_scratch(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -2023,87 +2068,6 @@ cudaError_t noalloc_scratch(unsigned long long** out) {
   }
   *out = static_cast<unsigned long long*>(g_noalloc_addr[dev]);
   return cudaSuccess;
-}
-
-// The digit plan of a configuration, into fixed-size arrays (no heap use).
-stats_status noalloc_plan(const stats_config* cfg, ColPlan (&cp)[kMaxCols], ExactParams& xp, int& conv) {
-  const int p = cfg->p;
-  const bool bounded = cfg->lo != nullptr;
-  for (int j = 0; j < p; ++j) {
-    const int32_t dt = cfg->dtypes[j];
-    if (dt < I16 || dt > F64) return STATS_EINVAL;
-    cp[j] = ColPlan{};
-    const double lo = bounded ? cfg->lo[j] : 0.0, hi = bounded ? cfg->hi[j] : 0.0;
-    const bool ok = (dt == F32 || dt == F64) ? real_field(bounded, lo, hi, cp[j]) : int_field(dt, bounded, lo, hi, cp[j]);
-    if (!ok) return STATS_EINVAL;
-  }
-  static const int32_t l32[12] = {I64, I32, I32, I32, I32, I32, I32, I32, F64, I32, F64, I32};
-  static const int32_t l16[12] = {I64, I16, I16, I16, I16, I32, I16, I16, F64, I16, F64, I16};
-  conv = CONV_GENERIC;
-  for (int layout = 0; layout < 2 && p == 12; ++layout) {
-    const int32_t* want = layout ? l16 : l32;
-    bool match = true;
-    for (int j = 0; j < 12; ++j) match = match && cfg->dtypes[j] == want[j];
-    for (int j : {1, 2, 3, 4, 6, 7, 11}) match = match && !cp[j].is_signed && cp[j].k == 1;
-    for (int j : {5, 9}) match = match && !cp[j].is_signed && cp[j].k <= 2;
-    match = match && !cp[0].is_signed && cp[0].k <= 5 && cp[8].is_real && cp[8].is_signed && cp[10].is_real &&
-            !cp[10].is_signed;
-    if (match) {
-      conv = layout ? CONV_T1_L16 : CONV_T1_L32;
-      static const int off[12] = {12, 1, 2, 3, 4, 8, 5, 6, 17, 10, 24, 7};
-      static const int kk[12] = {5, 1, 1, 1, 1, 2, 1, 1, 7, 2, 7, 1};
-      for (int j = 0; j < 12; ++j) {
-        cp[j].off = off[j];
-        cp[j].k = kk[j];
-      }
-      break;
-    }
-  }
-  if (conv == CONV_GENERIC) {
-    int slot = 1;
-    for (int j = 0; j < p; ++j) {
-      cp[j].off = slot;
-      slot += cp[j].k;
-    }
-    if (slot > kDigits) return STATS_EINVAL;
-    for (int q = 0; q < kDigitPairs; ++q) {
-      xp.pc0[q] = xp.pc1[q] = -2;
-      xp.pb0[q] = xp.pb1[q] = 0;
-      xp.ps0[q] = xp.ps1[q] = 0;
-    }
-    xp.pc0[0] = -1;
-    for (int j = 0; j < p; ++j)
-      for (int a = 0; a < cp[j].k; ++a) {
-        const int s = cp[j].off + a, q = s / 2;
-        const int8_t sg = (cp[j].is_signed && a == cp[j].k - 1) ? 1 : 0;
-        if (s & 1) {
-          xp.pc1[q] = static_cast<int8_t>(j);
-          xp.pb1[q] = static_cast<int8_t>(a);
-          xp.ps1[q] = sg;
-        } else {
-          xp.pc0[q] = static_cast<int8_t>(j);
-          xp.pb0[q] = static_cast<int8_t>(a);
-          xp.ps0[q] = sg;
-        }
-      }
-  }
-  int off = 0;
-  for (int j = 0; j < p; ++j) {
-    const int b = dtype_bytes(cfg->dtypes[j]);
-    xp.dtype[j] = cfg->dtypes[j];
-    xp.col_bytes[j] = b;
-    xp.col_off[j] = off;
-    off += stage_col_bytes(b);
-    xp.real_shift[j] = cp[j].shift;
-    xp.real_emax[j] = cp[j].emax;
-    xp.kbytes[j] = cp[j].k;
-    xp.is_signed[j] = cp[j].is_signed;
-  }
-  xp.p = p;
-  xp.stage_bytes = off;
-  xp.stages = exact_pick_stages(off);
-  if (xp.stages == 0) return STATS_EINVAL;
-  return STATS_OK;
 }
 
 }  // namespace
@@ -2121,7 +2085,7 @@ extern "C" stats_status stats_pass_noalloc(const stats_config* cfg, const void* 
   ColPlan cp[kMaxCols];
   ExactParams P{};
   int conv = CONV_GENERIC;
-  stats_status s = noalloc_plan(cfg, cp, P, conv);
+  stats_status s = exact_plan(cfg->p, cfg->dtypes, cfg->lo != nullptr, cfg->lo, cfg->hi, cp, P, conv);
   if (s != STATS_OK) return s;
   unsigned long long* scratch = nullptr;
   if (noalloc_scratch(&scratch) != cudaSuccess) return STATS_ECUDA;
@@ -2144,7 +2108,7 @@ extern "C" stats_status stats_pass_noalloc(const stats_config* cfg, const void* 
     P.nmain = P.direct ? nrows : (nrows & ~int64_t(7));
     int dev = 0, sms = 1;
     if (cudaGetDevice(&dev) != cudaSuccess) return STATS_ECUDA;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return STATS_ECUDA;
     const int per = std::max(1, exact_max_active_blocks(conv, P.stages, P.stage_bytes));
     const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
     const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(sms, 1)) * per,

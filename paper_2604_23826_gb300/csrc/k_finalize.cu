@@ -517,10 +517,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier of a cooperative launch.  Thread 0 of each block publishes the block's
 // writes (fence), arrives, and the last arrival resets the count and advances the
-// generation; the others poll the generation.  A poll that outlasts kGridWaitNs sets the
+// generation; the others poll the generation.  A poll that outlasts wait_ns sets the
 // shared error word; a block that sees it set leaves.  Returns false in every block once
 // the error is set.
-__device__ bool grid_sync(unsigned int* bar, unsigned int& gen, int* s_ok) {
+__device__ bool grid_sync(unsigned int* bar, unsigned int& gen, int* s_ok, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -535,7 +535,7 @@ __device__ bool grid_sync(unsigned int* bar, unsigned int& gen, int* s_ok) {
       const unsigned long long t0 = global_ns();
       while (ld_acquire_u32(&bar[1]) == g) {
         if (ld_acquire_u32(&bar[2]) != 0u) break;
-        if (global_ns() - t0 > kGridWaitNs) {
+        if (global_ns() - t0 > wait_ns) {
           atomicExch(&bar[2], 1u);
           break;
         }
@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
   __shared__ int s_ok;
   if (__ldcg(J.ctl) == 0) return;  // the finalize kernel found the eigenpairs undefined
   const int tid = threadIdx.x;
+  const unsigned long long wait_ns = J.wait_ns > 0 ? static_cast<unsigned long long>(J.wait_ns) : kGridWaitNs;
   const int pa = J.pa, m = J.m;
   const int nthreads = gridDim.x * kJacThreads;
   const int gtid = blockIdx.x * kJacThreads + tid;
@@ -628,6 +629,10 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
   double* B = J.b;
   double* V = J.v;
   double* flags = J.out + J.flags_off;
+  // a block told to be absent leaves before its first arrival: the other blocks' waits at
+  // that barrier run out after wait_ns and the call reports the timeout (the failure path
+  // of a stalled block, taken without a fault)
+  if (static_cast<int>(blockIdx.x) == J.absent_block) goto timed_out;
 
   // V = I, or the previous eigenvectors as columns
   for (int i = gtid; i < m * m; i += nthreads) {
@@ -636,11 +641,11 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
     if (J.basis && r < pa && c < pa) v = J.basis[static_cast<size_t>(c) * pa + r];
     __stcg(V + i, v);
   }
-  if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+  if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
   if (J.basis) {
     // the seed is used only if its columns are orthonormal: max |V^T V - I| <= 1e-9
     grid_matmul(V, V, J.w, m, true, s_x, s_y);
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     double dev = 0.0;
     for (int i = gtid; i < m * m; i += nthreads) {
       const double x = __ldcg(J.w + i) - ((i / m == i % m) ? 1.0 : 0.0);
@@ -655,7 +660,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
       for (int w = 0; w < kJacThreads / 32; ++w) d = fmax(d, s_red[w]);
       __stcg(J.slots + blockIdx.x, d);
     }
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     if (tid == 0) {
       double d = 0.0;
       for (int b = 0; b < static_cast<int>(gridDim.x); ++b) d = fmax(d, __ldcg(J.slots + b));
@@ -666,20 +671,20 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
     __syncthreads();
     if (!seeded) {  // cold start after all
       for (int i = gtid; i < m * m; i += nthreads) __stcg(V + i, (i / m == i % m) ? 1.0 : 0.0);
-      if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+      if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     }
   }
   if (seeded) {
     // A <- V^T A V, symmetrised: W = A V, B = V^T W, A = (B + B^T) / 2
     grid_matmul(A, V, J.w, m, false, s_x, s_y);
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     grid_matmul(V, J.w, B, m, true, s_x, s_y);
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     for (int i = gtid; i < m * m; i += nthreads) {
       const int r = i / m, c = i % m;
       __stcg(A + i, 0.5 * (__ldcg(B + static_cast<size_t>(r) * m + c) + __ldcg(B + static_cast<size_t>(c) * m + r)));
     }
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
   }
   {
     // ||A||_F^2 once; the off-diagonal part before every sweep
@@ -695,7 +700,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
       __stcg(J.slots + blockIdx.x, bf);
       __stcg(J.slots + gridDim.x + blockIdx.x, bo);
     }
-    if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+    if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     if (tid == 0) {
       double t = 0.0;
       for (int b = 0; b < static_cast<int>(gridDim.x); ++b) t += __ldcg(J.slots + b);
@@ -784,7 +789,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
           __stcg(B + static_cast<size_t>(gr) * m + gc, s_S[lr_][lc_]);
           __syncthreads();
         }
-        if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+        if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
         // (2) the other blocks of A, Q_P^T A[P rows][P' cols] Q_P' (into B), and V's columns,
         //     V[rows][P' cols] Q_P' (in place: every entry belongs to one item)
         const int nA = np * np, nItems = nA + (m / kJP) * np;
@@ -825,7 +830,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
         double* t = A;
         A = B;
         B = t;
-        if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+        if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
       }
       double lo2 = 0.0;
       for (int i = gtid; i < m * m; i += nthreads) {
@@ -834,7 +839,7 @@ __global__ void __launch_bounds__(kJacThreads, 1) jacobi_grid_kernel(const __gri
       }
       const double bo2 = block_sum(lo2, s_red);
       if (tid == 0) __stcg(J.slots + gridDim.x + blockIdx.x, bo2);
-      if (!grid_sync(J.bar, gen, &s_ok)) goto timed_out;
+      if (!grid_sync(J.bar, gen, &s_ok, wait_ns)) goto timed_out;
     }
     // descending order (ties by index), eigenvector signs: largest-magnitude component positive
     for (int c = tid; c < pa; c += kJacThreads) {

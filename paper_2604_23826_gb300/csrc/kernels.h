@@ -342,6 +342,8 @@ struct JacobiParams {
   double* out;              // finalize result buffer
   int64_t evals_off, evecs_off, flags_off;
   int32_t pa, m;            // analysis columns; m = pa rounded up to a multiple of 16
+  int64_t wait_ns;          // limit of one grid-wide wait (<= 0: 2 s)
+  int32_t absent_block;     // testing: this block leaves before its first arrival (-1: none)
 };
 // Doubles of scratch jacobi_grid_kernel needs for pa analysis columns (the five arrays above).
 size_t jacobi_scratch_doubles(int pa);

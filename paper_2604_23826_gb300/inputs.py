@@ -33,6 +33,22 @@ def many_tables_shapes(seed: int, ntables: int, n_lo: float = 1e3, n_hi: float =
     return params
 
 
+def check_sample(params, small_max: float = 1e6, n_small=None, n_large: int = 64):
+    """Indices of the many-tables workload picked for a check against the CPU oracle.
+
+    Every table of at most small_max rows (or n_small of them) and n_large of the larger
+    tables; a subset is stratified by row count (evenly spaced ranks in order of n, so the
+    whole range of sizes is represented), and the result is in table order."""
+    def spread(idx, k):
+        idx = sorted(idx, key=lambda t: (params[t][0], t))
+        if k is None or k >= len(idx):
+            return idx
+        return [idx[int(round(i * (len(idx) - 1) / max(1, k - 1)))] for i in range(k)]
+    small = [t for t, (n, _, _, _) in enumerate(params) if n <= small_max]
+    large = [t for t, (n, _, _, _) in enumerate(params) if n > small_max]
+    return sorted(set(spread(small, n_small)) | set(spread(large, n_large)))
+
+
 def gen_table(torch, n: int, p: int, mu, sd, seed: int, device, out=None):
     """[p, n] float32 on `device`: row j ~ N(mu_j, sd_j^2) (FP32 after the affine map)."""
     g = torch.Generator(device=device)

@@ -48,3 +48,24 @@ def combine_in_rank_order(parts: Sequence, load: Callable, merge: Callable):
     for part in parts[1:]:
         merge(acc, load(part))
     return acc
+
+
+def combine_contexts(ctx, group=None):
+    """The global statistics of every rank's context, on every rank.
+
+    Each rank exports its accumulator (stats_export: a few KB, the single exchange of
+    the data-parallel pass), the images are all-gathered in rank order, and each rank
+    imports them and merges them with stats_merge in rank order, so every rank holds
+    the same combination (bit-identical for STATS_EXACT; the shifted modes re-express
+    each image about the first one's pivot in double-double).  Returns a new context
+    owned by the caller."""
+    from . import binding as G
+
+    parts = gather_in_rank_order(G.stats_export(ctx), group)
+
+    def merge(acc, other):
+        G.stats_merge(acc, other)
+        G.stats_sync(acc)
+        other.close()
+
+    return combine_in_rank_order(parts, lambda blob: G.stats_import(blob, ctx.p, ctx.mode), merge)

@@ -96,3 +96,38 @@ def test_ranges_partition():
     assert shard.weak_range(5, 3) == (15, 5)
     with pytest.raises(ValueError):
         shard.strong_range(10, 0, 0)
+
+
+def _worker_leaves(rank, world, port, out_q):
+    """Rank 1 fails between steps (an exception before the gather, nothing in flight); rank 0
+    must learn of it from its next collective, which ends with an error instead of hanging."""
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    r0, n = shard.strong_range(2_000, world, rank)
+    st = O.stats_table1(17, n, row0=r0, threads=1)
+    if rank == 1:
+        raise SystemExit(3)  # the failing rank leaves without joining the gather
+    t0 = __import__("time").monotonic()
+    try:
+        shard.gather_in_rank_order({"n": st.n})
+        out_q.put(("no error", 0.0))
+    except Exception as e:  # noqa: BLE001 - the collective's own error type varies by transport
+        out_q.put((type(e).__name__, __import__("time").monotonic() - t0))
+
+
+def test_rank_that_leaves_is_detected_by_the_next_collective():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_leaves, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    kind, secs = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert kind != "no error"
+    assert secs < 60
+    assert procs[1].exitcode == 3
