@@ -72,6 +72,12 @@ def parse_args():
     ap.add_argument("--ntables", type=int, default=4096)
     ap.add_argument("--wave-gb", type=float, default=64.0)
     ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S")
+    ap.add_argument("--tune", choices=("off", "cached", "measure"), default="off",
+                    help="tables4096: batched-launch tuning (off: library defaults; cached: a cached choice for "
+                         "this device and library build, measured first if there is none; measure: re-measure on "
+                         "the first wave)")
+    ap.add_argument("--by-width", action="store_true",
+                    help="tables4096: also time each width class's tables alone (reported, not the headline)")
     ap.add_argument("--oracle-check", choices=("none", "quick", "full"), default="quick",
                     help="tables4096: tables compared with the CPU oracle (quick: 64 of <= 1e6 rows and 16 "
                          "larger, stratified by rows; full: every table of <= 1e6 rows and 64 larger); "
@@ -592,6 +598,16 @@ def run_tables(args, rank: int, world: int, local_rank: int):
             off += p * ld[t]
         return views
 
+    tuning = None
+    if args.tune != "off":
+        from paper_2604_23826_gb300 import tune
+        g0 = groups[0]
+        views = materialise(g0)
+        tuning = tune.autotune_batched([ctxs[t] for t in g0], [[x[j] for j in range(x.shape[0])] for x in views],
+                                       [params[t][0] for t in g0], stream=stream, workload=f"tables{args.ntables}",
+                                       force=args.tune == "measure")
+        for t in g0:
+            G.stats_reset(ctxs[t])
     wave_ms = []
     host_ms = []
     # per wave: one pivot launch + one batched launch per tile width present (32: p <= 32, 64: p = 64)
@@ -631,6 +647,44 @@ def run_tables(args, rank: int, world: int, local_rank: int):
         step(True)
     clocks = sampler.stop()
     ms = sum(wave_ms) / len(wave_ms)
+    by_width = None
+    if args.by_width:
+        # each width class's tables alone, wave by wave (the batched call then runs that class's
+        # launches only): where the step's time goes
+        by_width = {}
+        for w in (8, 16, 32, 64):
+            w_ms, w_bytes = 0.0, 0
+            for g in groups:
+                sel = [i for i, t in enumerate(g) if (8 if params[t][1] <= 8 else 16 if params[t][1] <= 16 else
+                                                      32 if params[t][1] <= 32 else 64) == w]
+                if not sel:
+                    continue
+                views = materialise(g)
+                tabs = [g[i] for i in sel]
+                for t in tabs:
+                    G.stats_reset(ctxs[t])
+                cols = [[views[i].data_ptr() + 4 * views[i].stride(0) * j for j in range(views[i].shape[0])]
+                        for i in sel]
+                batch = G.BatchArgs([ctxs[t] for t in tabs], cols, [params[t][0] for t in tabs])
+                best = float("inf")
+                for _ in range(3):
+                    for t in tabs:
+                        G.stats_reset(ctxs[t])
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    G.stats_accumulate_batched(batch, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                w_ms += best
+                w_bytes += sum(4 * params[t][0] * params[t][1] for t in tabs)
+            pk = measured_peaks().get("hbm_gbs") or 6800.0
+            by_width[w] = {"ms": w_ms, "bytes": w_bytes, "GB_per_s": w_bytes / (w_ms / 1e3) / 1e9,
+                           "frac": w_bytes / (w_ms / 1e3) / 1e9 / pk, "share_of_step": w_ms / ms}
+        # the contexts hold partial rows now: one more full step restores every table's statistics
+        step(False)
     # finalize of every table (reported, outside the pass time): one batched call
     f0 = time.perf_counter()
     finals = G.stats_finalize_batched([ctxs[t] for t in mine])
@@ -690,13 +744,13 @@ def run_tables(args, rank: int, world: int, local_rank: int):
               "l2": "inputs larger than L2 (no flush)", "parallelism": f"tables dealt to {world} rank(s)"}
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
-            "kernel": "gram32_kernel (register-fragment mma.sync bf16)" if mode_name.startswith("BF16")
-            else MODE_KERNEL[mode_name],
+            "kernel": "narrow_kernel (tcgen05; 33-64 columns, 53 % of the bytes) + gram32_kernel (mma.sync; 1-32 "
+                      "columns)" if mode_name.startswith("BF16") else MODE_KERNEL[mode_name],
             "kernel_ms": ms, "algorithmic_bytes": bytes_total}
     extra = {"finalize_ms_all_tables_batched": fin_ms,
              "host_ms_per_call": sum(host_ms) / max(1, len(host_ms)),
              "check_means_within_sqrt_n_sigma_units": worst_mean_rel,
-             "oracle_check": oracle_check}
+             "oracle_check": oracle_check, "tuning": tuning, "by_width": by_width}
     out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, batched FP32 tables",
                      rows_all / (ms_all / 1e3), ms_all, config, roof, clocks,
                      launches_per_step * args.steps, extra)

@@ -280,6 +280,28 @@ int32_t stats_num_analysis_columns(const stats_ctx* ctx);
  * STATS_EXACT do not depend on it.  Errors: EINVAL (negative). */
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks);
 
+/* How stats_accumulate_batched deals the stages of its split-mode tables to the persistent
+ * CTAs of a launch, per width class (tables of 1-8, 9-16, 17-32 and 33-64 columns) and mode
+ * (STATS_BF16X3, STATS_BF16X4).  The autotuner in paper_2604_23826_gb300/tune.py measures
+ * candidate settings on a batch and sets the fastest.
+ *   narrow_units_per_cta   33-64 columns in [p, ld] blocks (the persistent tcgen05 launch):
+ *                          tables are cut into units of 64-row stages, sized so that each CTA
+ *                          gets about this many units (1..256; default 12)
+ *   gram32_chunks_per_cta  the register-fragment launch: stages are dealt in chunks, as long
+ *                          as possible while each CTA gets at least this many (1..1024;
+ *                          default 32)
+ *   gram32_min_chunk       ... and never shorter than this many stages (1..65536; default 32)
+ * The setting changes how rows are grouped into per-CTA partial sums, so results move within
+ * rounding (the stated tolerance holds for every setting); a fixed setting reproduces its
+ * bits.  Process-wide, for every device.  Errors: EINVAL (bad width, mode or values). */
+typedef struct {
+  int32_t narrow_units_per_cta;
+  int32_t gram32_chunks_per_cta;
+  int32_t gram32_min_chunk;
+} stats_batch_tuning;
+stats_status stats_set_batch_tuning(int32_t width, int32_t mode, const stats_batch_tuning* t);
+stats_status stats_get_batch_tuning(int32_t width, int32_t mode, stats_batch_tuning* t);
+
 /* Testing knob of the bounded grid-wide waits of the eigen-solver that stats_finalize and
  * stats_finalize_warm run over the whole GPU (more than 23 analysis columns, or a seed).
  *   wait_ns       how long a block waits at a grid barrier before the call gives up with

@@ -295,6 +295,30 @@ def stats_set_flush_rows(ctx: Ctx, rows: int):
     _check(L.stats_set_flush_rows(ctx.handle, rows), "stats_set_flush_rows")
 
 
+class _BatchTuning(ctypes.Structure):
+    _fields_ = [("narrow_units_per_cta", ctypes.c_int32), ("gram32_chunks_per_cta", ctypes.c_int32),
+                ("gram32_min_chunk", ctypes.c_int32)]
+
+
+def stats_set_batch_tuning(width: int, mode: int, t: dict):
+    """How batched launches of a width class (1-8, 9-16, 17-32, 33-64 columns) and split mode
+    deal their stages to CTAs (stats.h); t has the three stats_batch_tuning fields."""
+    L = load()
+    L.stats_set_batch_tuning.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_BatchTuning)]
+    L.stats_set_batch_tuning.restype = ctypes.c_int
+    v = _BatchTuning(int(t["narrow_units_per_cta"]), int(t["gram32_chunks_per_cta"]), int(t["gram32_min_chunk"]))
+    _check(L.stats_set_batch_tuning(width, mode, ctypes.byref(v)), "stats_set_batch_tuning")
+
+
+def stats_get_batch_tuning(width: int, mode: int) -> dict:
+    L = load()
+    L.stats_get_batch_tuning.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_BatchTuning)]
+    L.stats_get_batch_tuning.restype = ctypes.c_int
+    v = _BatchTuning()
+    _check(L.stats_get_batch_tuning(width, mode, ctypes.byref(v)), "stats_get_batch_tuning")
+    return {f: getattr(v, f) for f, _ in _BatchTuning._fields_}
+
+
 def stats_set_grid_wait(ctx: Ctx, wait_ns: int = 0, absent_block: int = -1):
     """Limit of the eigen-solver's bounded grid-wide waits (0: 2 s), and optionally a block that
     leaves before arriving, so that the other blocks' waits run out (stats.h)."""

@@ -355,6 +355,29 @@ struct Gram32Job {
   bool x4;  // all four products (BF16x4, or a BF16x3 context still below its row threshold)
 };
 
+// Tuning of the batched launches, per width class (P = 8, 16, 32, 64) and arithmetic (BF16x3,
+// BF16x4): how a launch's stages are dealt to its persistent CTAs.  Set by stats_set_batch_tuning
+// (the autotuner); the defaults were measured on the many-tables workload.
+stats_batch_tuning g_batch_tuning[4][2];
+std::once_flag g_batch_tuning_once;
+std::mutex g_batch_tuning_mu;
+
+int width_class(int P) { return P <= 8 ? 0 : P <= 16 ? 1 : P <= 32 ? 2 : 3; }
+
+stats_batch_tuning batch_tuning(int P, bool x4) {
+  std::call_once(g_batch_tuning_once, [] {
+    for (auto& row : g_batch_tuning)
+      for (auto& t : row) t = stats_batch_tuning{12, 32, 32};
+  });
+  std::lock_guard<std::mutex> lk(g_batch_tuning_mu);
+  return g_batch_tuning[width_class(P)][x4 ? 1 : 0];
+}
+
+bool valid_tuning(const stats_batch_tuning& t) {
+  return t.narrow_units_per_cta >= 1 && t.narrow_units_per_cta <= 256 && t.gram32_chunks_per_cta >= 1 &&
+         t.gram32_chunks_per_cta <= 1024 && t.gram32_min_chunk >= 1 && t.gram32_min_chunk <= 65536;
+}
+
 struct Gram32Workspace {
   void* dev = nullptr;
   size_t bytes = 0;
@@ -455,9 +478,10 @@ stats_status run_gram32(const std::vector<Gram32Job>& jobs, cudaStream_t st) {
         int64_t total = 0;
         for (size_t i = 0; i < nt; ++i) total += (all[first + i]->nrows + rs - 1) / rs;
         if (total >= (int64_t(1) << 31)) return STATS_EINVAL;  // over 2^31 stages in one call
-        // chunks as long as possible while every CTA still gets >= kGram32ChunksPerCta of them
-        // (long runs: few per-table partials; many chunks: balanced CTAs)
-        const int64_t K = std::max<int64_t>(kGram32Chunk, total / (int64_t(sms) * kGram32ChunksPerCta));
+        // chunks as long as possible while every CTA still gets >= chunks_per_cta of them (long
+        // runs: few per-table partials; many chunks: balanced CTAs), and never below min_chunk
+        const stats_batch_tuning tune = batch_tuning(P, x4 == 1);
+        const int64_t K = std::max<int64_t>(tune.gram32_min_chunk, total / (int64_t(sms) * tune.gram32_chunks_per_cta));
         const int grid = static_cast<int>(std::min<int64_t>((total + K - 1) / K, sms));
         const size_t sf = gram32_slot_floats(P);
         size_t slot_floats_total = 0;
@@ -709,10 +733,9 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
 
 // Tables of 33..64 FP32 columns of one batched call, one mode: a single persistent narrow
 // launch.  Each table is cut into units of at most U stages, U chosen so that the CTAs get
-// about kNarrowUnitsPerCta units each (a unit runs on one SM: large units would leave the
+// about narrow_units_per_cta units each (a unit runs on one SM: large units would leave the
 // last CTAs finishing alone); units are dealt to CTAs largest first (CTA b takes units b,
 // b + grid, ...), and every unit has its own slot, merged per table in row order.
-constexpr int kNarrowUnitsPerCta = 12;
 constexpr int64_t kNarrowUnitMinStages = 64, kNarrowUnitMaxStages = 16384;
 
 struct NarrowJob {
@@ -744,9 +767,9 @@ stats_status run_narrow_batch(const std::vector<NarrowJob>& jobs, bool x4, cudaS
   std::vector<int> need_shift;
   int64_t total = 0;
   for (const NarrowJob& j : jobs) total += (j.nrows + rs - 1) / rs;
-  const int64_t ustages = std::min(kNarrowUnitMaxStages,
-                                   std::max(kNarrowUnitMinStages, total / (int64_t(std::max(1, c0->sms)) *
-                                                                           kNarrowUnitsPerCta)));
+  const int64_t ustages =
+      std::min(kNarrowUnitMaxStages, std::max(kNarrowUnitMinStages, total / (int64_t(std::max(1, c0->sms)) *
+                                                                             batch_tuning(64, x4).narrow_units_per_cta)));
   for (size_t i = 0; i < nt; ++i) {
     const NarrowJob& j = jobs[i];
     tabs[i] = narrow_table(j.c, j.cols, j.nrows);
@@ -1969,6 +1992,21 @@ const char* stats_strerror(stats_status st) {
 }
 
 int32_t stats_num_analysis_columns(const stats_ctx* ctx) { return ctx ? ctx->pa : -1; }
+
+stats_status stats_set_batch_tuning(int32_t width, int32_t mode, const stats_batch_tuning* t) {
+  if (!t || width < 1 || width > 64 || (mode != STATS_BF16X3 && mode != STATS_BF16X4) || !valid_tuning(*t))
+    return STATS_EINVAL;
+  (void)batch_tuning(width, mode == STATS_BF16X4);  // defaults in place first
+  std::lock_guard<std::mutex> lk(g_batch_tuning_mu);
+  g_batch_tuning[width_class(width)][mode == STATS_BF16X4 ? 1 : 0] = *t;
+  return STATS_OK;
+}
+
+stats_status stats_get_batch_tuning(int32_t width, int32_t mode, stats_batch_tuning* t) {
+  if (!t || width < 1 || width > 64 || (mode != STATS_BF16X3 && mode != STATS_BF16X4)) return STATS_EINVAL;
+  *t = batch_tuning(width, mode == STATS_BF16X4);
+  return STATS_OK;
+}
 
 stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent_block) {
   if (!ctx || wait_ns < 0 || wait_ns > int64_t(60) * 1000000000 || absent_block < -1) return STATS_EINVAL;

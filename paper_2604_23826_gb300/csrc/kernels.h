@@ -154,8 +154,6 @@ struct Gram32Launch {
   int32_t chunk;             // consecutive stages dealt to one CTA (chunk c goes to CTA c % grid)
   int32_t flush_kblocks;     // 16-row K blocks between FP32 -> (hi, lo) flushes
 };
-constexpr int kGram32Chunk = 32;         // smallest chunk (stages)
-constexpr int kGram32ChunksPerCta = 32;  // chunks a CTA gets at least, when the launch is large enough
 int gram32_width(int p);                 // P = 8, 16, 32 or 64
 size_t gram32_slot_floats(int P);        // floats of one warp / unit slot
 int gram32_rows_per_stage(int P);
