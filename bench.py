@@ -64,6 +64,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
+    ap.add_argument("--exact-shape", type=int, default=-1,
+                    help="launch shape of the exact pass (-1: the library default; 0, 1, 2: stats.h)")
     ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10", "table1_file",
                                                 "table1_csv"),
                     default="table1",
@@ -335,6 +337,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cfg = G.stats_table1_config(layout, world * n, G.STATS_EXACT)
     ctx = G.stats_init(cfg)
+    G.stats_set_exact_shape(ctx, args.exact_shape)
     pass_events = []
     from paper_2604_23826_gb300 import shard
     combined = {}
@@ -522,6 +525,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"table1_n{n:.0e}_seed{SEED}_{args.layout}".replace("+", ""), "rows_per_gpu": n,
                    "p": 12, "layout": args.layout, "bytes_per_row": bpr, "mode": "STATS_EXACT",
+                   "exact_shape": args.exact_shape,
                    "step": "exact fused pass + finalize (mean, cov, corr, PCA) + D2H of the result",
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"rows sharded over {world} rank(s)" + (

@@ -316,6 +316,15 @@ stats_status stats_get_batch_tuning(int32_t width, int32_t mode, stats_batch_tun
  * Applies to later finalize calls on ctx.  Errors: EINVAL. */
 stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent_block);
 
+/* Launch shape of the STATS_EXACT pass (-1 = the library's default for the ctx's converter):
+ *   0  15 consumer warps, 64 rows each per stage (960-row stages)
+ *   1  19 consumer warps, 32 rows each (608-row stages)
+ *   2  23 consumer warps, 32 rows each (736-row stages)
+ * More warps hide more latency per SM but get fewer registers and smaller stages.  Results
+ * do not depend on the shape (integer accumulation).  Errors: EINVAL (unknown shape, or the
+ * ctx's rows do not fit that shape's pipeline). */
+stats_status stats_set_exact_shape(stats_ctx* ctx, int32_t shape);
+
 /* Tuning knob of STATS_BF16X3 / STATS_BF16X4 (16..4096, a multiple of 16): rows of
  * round-to-nearest FP32 accumulation of a warp before its (hi, lo) pairs (default
  * 1024 for p > 64, 16384 for p <= 64).  Every 16-row block is a fresh tensor-core

@@ -319,6 +319,14 @@ def stats_get_batch_tuning(width: int, mode: int) -> dict:
     return {f: getattr(v, f) for f, _ in _BatchTuning._fields_}
 
 
+def stats_set_exact_shape(ctx: Ctx, shape: int):
+    """Launch shape of the STATS_EXACT pass (-1: default; 0, 1, 2: see stats.h)."""
+    L = load()
+    L.stats_set_exact_shape.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.stats_set_exact_shape.restype = ctypes.c_int
+    _check(L.stats_set_exact_shape(ctx.handle, shape), "stats_set_exact_shape")
+
+
 def stats_set_grid_wait(ctx: Ctx, wait_ns: int = 0, absent_block: int = -1):
     """Limit of the eigen-solver's bounded grid-wide waits (0: 2 s), and optionally a block that
     leaves before arriving, so that the other blocks' waits run out (stats.h)."""

@@ -89,6 +89,7 @@ struct stats_ctx {
   unsigned int* d_split_ticket = nullptr;
   int split_grid = 0;
   int flush_rows = 0;                   // 0: by table width
+  int exact_shape = -1;                 // EXACT launch shape (-1: the converter's default)
   int64_t grid_wait_ns = 0;             // eigen-solver grid waits: limit (0: 2 s)
   int32_t grid_absent_block = -1;       // testing: a block of the eigen-solver that never arrives
   // the last 2D tensor map made for this ctx's FP32 columns (reused while the layout is the same)
@@ -187,6 +188,13 @@ bool real_field(bool bounded, double lo, double hi, ColPlan& cp) {
   return true;
 }
 
+// The launch shape of the exact pass used unless a ctx asks for another (stats_set_exact_shape):
+// per converter, the fastest measured on a GB300.
+int exact_default_shape(int conv) {
+  (void)conv;
+  return 0;
+}
+
 // Whether a column plan is one of the Table 1 layouts that the specialised converters read
 // (the dtypes of the layout, and digit fields no wider than the converter handles).
 bool is_t1_plan(int p, const int32_t* dtypes, const ColPlan* cp, int layout) {
@@ -264,22 +272,16 @@ stats_status exact_plan(int p, const int32_t* dtypes, bool bounded, const double
       xp.ps1[q] = sg[2 * q + 1];
     }
   }
-  int off = 0;
   for (int j = 0; j < p; ++j) {
-    const int b = dtype_bytes(dtypes[j]);
     xp.dtype[j] = dtypes[j];
-    xp.col_bytes[j] = b;
-    xp.col_off[j] = off;
-    off += stage_col_bytes(b);
+    xp.col_bytes[j] = dtype_bytes(dtypes[j]);
     xp.real_shift[j] = cp[j].shift;
     xp.real_emax[j] = cp[j].emax;
     xp.kbytes[j] = cp[j].k;
     xp.is_signed[j] = cp[j].is_signed;
   }
   xp.p = p;
-  xp.stage_bytes = off;
-  xp.stages = exact_pick_stages(off);
-  if (xp.stages == 0) return STATS_EINVAL;  // rows too wide for the pipeline
+  if (!exact_layout(xp, exact_default_shape(conv))) return STATS_EINVAL;  // rows too wide for the pipeline
   return STATS_OK;
 }
 
@@ -310,7 +312,7 @@ stats_status device_status(stats_ctx* c) {
 int default_grid(stats_ctx* c) {
   if (c->grid > 0) return c->grid;
   if (c->mode == STATS_EXACT) {
-    int per = exact_max_active_blocks(c->conv, c->stages, c->xp.stage_bytes);
+    int per = exact_max_active_blocks(c->conv, c->xp.shape, c->xp.stages, c->xp.stage_bytes);
     if (per < 1) per = 1;
     return c->sms * per;
   }
@@ -841,6 +843,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
   const int grid = default_grid(c);
   if (c->mode == STATS_EXACT) {
     ExactParams P = c->xp;
+    if (c->exact_shape >= 0 && c->exact_shape != P.shape && !exact_layout(P, c->exact_shape)) return STATS_EINVAL;
     P.direct = 0;
     for (int j = 0; j < c->p; ++j) {
       P.cols[j] = dcols[j];
@@ -848,8 +851,9 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     }
     P.nrows = nrows;
     P.nmain = P.direct ? nrows : (nrows & ~int64_t(7));
-    const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
-    int g = static_cast<int>(std::min<int64_t>(grid, std::max<int64_t>(tiles, 1)));
+    int g = grid;
+    if (c->grid <= 0 && P.shape != c->xp.shape)
+      g = c->sms * std::max(1, exact_max_active_blocks(c->conv, P.shape, P.stages, P.stage_bytes));
     CK(c, launch_exact(P, c->conv, g, st));
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && c->p <= 64 && nrows >= kNarrowMinRows &&
              narrow_eligible(c, dcols, nrows)) {
@@ -2015,6 +2019,16 @@ stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent
   return STATS_OK;
 }
 
+stats_status stats_set_exact_shape(stats_ctx* ctx, int32_t shape) {
+  if (!ctx || shape < -1 || shape >= kExactShapes) return STATS_EINVAL;
+  if (ctx->mode == STATS_EXACT && shape >= 0) {
+    ExactParams P = ctx->xp;
+    if (!exact_layout(P, shape)) return STATS_EINVAL;
+  }
+  ctx->exact_shape = shape;
+  return STATS_OK;
+}
+
 stats_status stats_set_grid(stats_ctx* ctx, int32_t blocks) {
   if (!ctx || blocks < 0) return STATS_EINVAL;
   ctx->grid = blocks;
@@ -2147,11 +2161,8 @@ extern "C" stats_status stats_pass_noalloc(const stats_config* cfg, const void* 
     int dev = 0, sms = 1;
     if (cudaGetDevice(&dev) != cudaSuccess) return STATS_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return STATS_ECUDA;
-    const int per = std::max(1, exact_max_active_blocks(conv, P.stages, P.stage_bytes));
-    const int64_t tiles = (P.nmain + kExactTile - 1) / kExactTile;
-    const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(std::max(sms, 1)) * per,
-                                                        std::max<int64_t>(tiles, 1)));
-    if (launch_exact(P, conv, grid, st) != cudaSuccess) return STATS_ECUDA;
+    const int per = std::max(1, exact_max_active_blocks(conv, P.shape, P.stages, P.stage_bytes));
+    if (launch_exact(P, conv, std::max(sms, 1) * per, st) != cudaSuccess) return STATS_ECUDA;
   }
   // recombination into the caller's buffer (all columns flagged identifiers: raw outputs only)
   FinalParams F{};

@@ -10,20 +10,24 @@
 // (every digit |d| <= 255 is exact in f16) and FP32 accumulators.  Each product
 // is below 2^16 and a warp flushes its accumulators every 256 of its rows, so
 // every partial sum is an integer below 2^24 and FP32 never rounds.  Flushes go
-// to int32 registers, then to an int64 block accumulator in shared memory, then
-// by integer atomics to a per-call int64 accumulator, which the last block to
+// by shared-memory integer atomics to an int64 block accumulator, then by global
+// integer atomics to a per-call int64 accumulator, which the last block to
 // finish adds to the context accumulator (integer addition: the result does not
-// depend on block order).  S_jk = sum_{a,b} 256^(a+b) G[(j,a),(k,b)] is
+// depend on block order or on the shape of the launch).  S_jk = sum_{a,b} 256^(a+b) G[(j,a),(k,b)] is
 // recombined exactly by the finalize kernel.
 //
-// Pipeline: one producer warp moves each 960-row stage of every column from
-// HBM to shared memory with bulk copies (cp.async.bulk, completion on an
-// mbarrier; columns whose address is not 16-byte aligned are instead read by
-// the consumers with plain loads); 15 consumer warps turn their 64 rows into digits, stage them as a
-// swizzled [32 rows x 32 digits] f16 tile, load operand fragments with
-// ldmatrix.trans and issue mma.sync m16n8k16 for the 6 upper-triangle 16x8
-// tiles of the 32x32 digit Gram.  All waits are bounded; an expired wait marks
-// the call failed (the accumulator is then left unchanged).
+// Pipeline: one producer warp moves each stage of every column from HBM to
+// shared memory with bulk copies (cp.async.bulk, completion on an mbarrier;
+// columns whose address is not 16-byte aligned are instead read by the consumers
+// with plain loads); W consumer warps take RPW rows of a stage each, turn them
+// into digits 32 rows at a time, stage those as a swizzled [32 rows x 32 digits]
+// f16 tile, load operand fragments with ldmatrix.trans and issue mma.sync
+// m16n8k16 for the 6 upper-triangle 16x8 tiles of the 32x32 digit Gram.  The
+// shape (W, RPW) is a launch choice (exact_shape_warps / exact_shape_rpw): more warps hide more latency
+// but need fewer registers each and smaller stages.  All waits are bounded; an
+// expired wait marks the call failed (the accumulator is then left unchanged).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,11 +35,8 @@ namespace ss {
 
 namespace {
 
-constexpr int kWarps = kExactWarps;
-constexpr int kTile = kExactTile;
 constexpr int kDigitTileBytes = 32 * 64;  // 32 rows x 32 f16 digits
 constexpr int kFlushRows = 256;           // per warp: FP32 partial sums stay below 2^24
-constexpr int kI32Flushes = 64;           // int32 partial sums stay below 2^30
 
 // ---- sources of raw column values: a shared-memory stage or global memory ----
 struct SmemSrc {
@@ -68,25 +69,25 @@ struct GlobalSrc {
   __device__ __forceinline__ float f32(int j) const { return static_cast<const float*>(P->cols[j])[r]; }
 };
 
-// Stage layout of the Table 1 layouts, known at compile time (the host lays a
-// stage out with the same rule: columns in order, stage_col_bytes() each).
-template <bool L16>
+// Stage layout of the Table 1 layouts for a stage of TILE rows, known at compile time
+// (the host lays a stage out with the same rule: columns in order, stage_col_bytes() each).
+template <bool L16, int TILE>
 struct T1Layout {
   __host__ __device__ static constexpr int bytes(int j) { return (j == 0 || j == 8 || j == 10) ? 8 : (L16 && j != 5) ? 2 : 4; }
   __host__ __device__ static constexpr int off(int j) {
     int o = 0;
-    for (int i = 0; i < j; ++i) o += stage_col_bytes(bytes(i));
+    for (int i = 0; i < j; ++i) o += stage_col_bytes(bytes(i), TILE);
     return o;
   }
 };
-template <bool L16>
+template <bool L16, int TILE>
 struct SmemT1Src {
   const uint8_t* base;  // stage base
   int r;                // row inside the stage
-  __device__ __forceinline__ int32_t i32(int j) const { return *reinterpret_cast<const int32_t*>(base + T1Layout<L16>::off(j) + r * 4); }
-  __device__ __forceinline__ int32_t i16(int j) const { return *reinterpret_cast<const int16_t*>(base + T1Layout<L16>::off(j) + r * 2); }
-  __device__ __forceinline__ int64_t i64(int j) const { return *reinterpret_cast<const int64_t*>(base + T1Layout<L16>::off(j) + r * 8); }
-  __device__ __forceinline__ double f64(int j) const { return *reinterpret_cast<const double*>(base + T1Layout<L16>::off(j) + r * 8); }
+  __device__ __forceinline__ int32_t i32(int j) const { return *reinterpret_cast<const int32_t*>(base + T1Layout<L16, TILE>::off(j) + r * 4); }
+  __device__ __forceinline__ int32_t i16(int j) const { return *reinterpret_cast<const int16_t*>(base + T1Layout<L16, TILE>::off(j) + r * 2); }
+  __device__ __forceinline__ int64_t i64(int j) const { return *reinterpret_cast<const int64_t*>(base + T1Layout<L16, TILE>::off(j) + r * 8); }
+  __device__ __forceinline__ double f64(int j) const { return *reinterpret_cast<const double*>(base + T1Layout<L16, TILE>::off(j) + r * 8); }
 };
 
 // The Table 1 real columns convert on the FP64 unit: q = round-to-nearest-even(x * 2^sh),
@@ -107,8 +108,9 @@ __device__ __forceinline__ uint64_t fixed_f2i(double x, int sh) {
 // The field checks below are exactly the ranges those digit fields can carry.
 template <bool L16>
 struct ConvT1 {
-  __device__ __forceinline__ static SmemT1Src<L16> smem_src(const uint8_t* st, const ExactParams&, int r) {
-    return SmemT1Src<L16>{st, r};
+  template <int TILE>
+  __device__ __forceinline__ static SmemT1Src<L16, TILE> smem_src(const uint8_t* st, const ExactParams&, int r) {
+    return SmemT1Src<L16, TILE>{st, r};
   }
   template <class Src>
   __device__ __forceinline__ static void row(const ExactParams& P, const Src& src, uint32_t (&w)[16],
@@ -168,6 +170,7 @@ __device__ __forceinline__ int64_t load_as_int(const ExactParams& P, const Src& 
 }
 
 struct ConvGeneric {
+  template <int TILE>
   __device__ __forceinline__ static SmemSrc smem_src(const uint8_t* st, const ExactParams& P, int r) {
     return SmemSrc{st, &P, r};
   }
@@ -227,7 +230,6 @@ __host__ __device__ constexpr int tile_j(int e) { return e < 4 ? e : e - 2; }
 
 struct WarpAcc {
   float f[6][4];
-  int32_t i[6][4];
 };
 
 // One 32-row sub-step of a warp: stage the digits, two K=16 blocks of MMAs.
@@ -255,17 +257,9 @@ __device__ __forceinline__ void warp_mma_32rows(uint32_t tile, int lane, const u
   __syncwarp();
 }
 
-__device__ __forceinline__ void flush_f32(WarpAcc& acc) {
-#pragma unroll
-  for (int e = 0; e < 6; ++e)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      acc.i[e][r] += __float2int_rn(acc.f[e][r]);
-      acc.f[e][r] = 0.f;
-    }
-}
-
-__device__ __forceinline__ void flush_i32(WarpAcc& acc, unsigned long long* cta_acc, int lane) {
+// FP32 accumulators (exact integers below 2^24) into the block's int64 accumulator in
+// shared memory: upper-triangle entries only, by integer atomics (order-independent).
+__device__ __forceinline__ void flush_to_block(WarpAcc& acc, unsigned long long* cta_acc, int lane) {
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int e = 0; e < 6; ++e)
@@ -273,18 +267,20 @@ __device__ __forceinline__ void flush_i32(WarpAcc& acc, unsigned long long* cta_
     for (int r = 0; r < 4; ++r) {
       const int row = 16 * tile_i(e) + g + ((r >> 1) << 3);
       const int col = 8 * tile_j(e) + 2 * t + (r & 1);
-      if (row <= col && acc.i[e][r] != 0)
-        atomicAdd(&cta_acc[row * kDigits + col], static_cast<unsigned long long>(static_cast<long long>(acc.i[e][r])));
-      acc.i[e][r] = 0;
+      const int v = __float2int_rn(acc.f[e][r]);
+      if (row <= col && v != 0)
+        atomicAdd(&cta_acc[row * kDigits + col], static_cast<unsigned long long>(static_cast<long long>(v)));
+      acc.f[e][r] = 0.f;
     }
 }
 
-template <class Conv>
-__global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __grid_constant__ ExactParams P) {
+template <class Conv, int W, int RPW>
+__global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __grid_constant__ ExactParams P) {
+  constexpr int kTile = W * RPW;  // rows of a stage
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* stage_base = smem;
   uint8_t* dtiles = smem + P.stages * P.stage_bytes;
-  unsigned long long* cta_acc = reinterpret_cast<unsigned long long*>(dtiles + kWarps * kDigitTileBytes);
+  unsigned long long* cta_acc = reinterpret_cast<unsigned long long*>(dtiles + W * kDigitTileBytes);
   uint64_t* full = reinterpret_cast<uint64_t*>(cta_acc + kDigits * kDigits);
   uint64_t* empty = full + kExactMaxStages;
   __shared__ uint32_t s_bad;
@@ -300,7 +296,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
     s_bad = 0;
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kWarps);
+      mbar_init(&empty[s], W);
     }
     fence_mbar_init();
   }
@@ -308,7 +304,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
 
   uint32_t bad = 0;       // range violations seen by this thread
   uint32_t failed = 0;    // a bounded wait expired
-  if (warp == kWarps) {
+  if (warp == W) {
     // ---------------- producer: bulk copies of every column of each stage ----------------
     if (lane == 0 && !P.direct) {
       int64_t issued = 0;
@@ -346,12 +342,9 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
 #pragma unroll
     for (int e = 0; e < 6; ++e)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        acc.f[e][r] = 0.f;
-        acc.i[e][r] = 0;
-      }
+      for (int r = 0; r < 4; ++r) acc.f[e][r] = 0.f;
     const uint32_t tile = smem_u32(dtiles + warp * kDigitTileBytes);
-    int sub = 0, flushes = 0;
+    int sub = 0;
     int s = 0;
     uint32_t ph = 0;  // phase parity of stage s's current use
     int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTile;
@@ -364,14 +357,14 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
       const int valid = static_cast<int>(min(static_cast<int64_t>(kTile), P.nmain - row0));
       const uint8_t* st = stage_base + s * P.stage_bytes;
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const int r = warp * 64 + h * 32 + lane;
+      for (int h = 0; h < RPW / 32; ++h) {
+        const int r = warp * RPW + h * 32 + lane;
         uint32_t w[16];
         if (r < valid && P.direct) {
           GlobalSrc src{&P, row0 + r};
           Conv::row(P, src, w, bad);
         } else if (r < valid) {
-          Conv::row(P, Conv::smem_src(st, P, r), w, bad);
+          Conv::row(P, Conv::template smem_src<kTile>(st, P, r), w, bad);
         } else {
 #pragma unroll
           for (int q = 0; q < 16; ++q) w[q] = 0u;
@@ -379,11 +372,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
         warp_mma_32rows(tile, lane, w, acc);
         if (++sub == kFlushRows / 32) {
           sub = 0;
-          flush_f32(acc);
-          if (++flushes == kI32Flushes) {
-            flushes = 0;
-            flush_i32(acc, cta_acc, lane);
-          }
+          flush_to_block(acc, cta_acc, lane);
         }
       }
       __syncwarp();
@@ -406,8 +395,7 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
       }
       warp_mma_32rows(tile, lane, w, acc);
     }
-    flush_f32(acc);
-    flush_i32(acc, cta_acc, lane);
+    flush_to_block(acc, cta_acc, lane);
   }
   if (bad) atomicOr(&s_bad, DEV_ERANGE);
   if (failed) atomicOr(&s_bad, DEV_ETIMEOUT);
@@ -443,56 +431,91 @@ __global__ void __launch_bounds__(kExactThreads, 1) exact_pass_kernel(const __gr
   }
 }
 
-template <class Conv>
+template <class Conv, int W, int RPW>
 cudaError_t launch_conv(const ExactParams& P, int grid, cudaStream_t stream) {
-  const size_t smem = exact_smem_bytes(P.stages, P.stage_bytes);
-  cudaError_t e = cudaFuncSetAttribute(exact_pass_kernel<Conv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  const size_t smem = exact_smem_bytes(P.shape, P.stages, P.stage_bytes);
+  auto* fn = exact_pass_kernel<Conv, W, RPW>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  exact_pass_kernel<Conv><<<grid, kExactThreads, smem, stream>>>(P);
+  fn<<<grid, (W + 1) * 32, smem, stream>>>(P);
   return cudaGetLastError();
 }
 
-template <class Conv>
+template <class Conv, int W, int RPW>
 int max_active(size_t smem) {
-  if (cudaFuncSetAttribute(exact_pass_kernel<Conv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
+  auto* fn = exact_pass_kernel<Conv, W, RPW>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, exact_pass_kernel<Conv>, kExactThreads, smem) !=
-      cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, (W + 1) * 32, smem) != cudaSuccess) return 0;
   return n;
 }
 
+// The kernel of a (converter, shape) pair: F<Conv, W, RPW>::run(args...).
+template <template <class, int, int> class F, class... A>
+auto dispatch(int conv, int shape, A... a) {
+  switch (conv * kExactShapes + shape) {
+    case CONV_T1_L32 * kExactShapes + 0: return F<ConvT1<false>, exact_shape_warps(0), exact_shape_rpw(0)>::run(a...);
+    case CONV_T1_L32 * kExactShapes + 1: return F<ConvT1<false>, exact_shape_warps(1), exact_shape_rpw(1)>::run(a...);
+    case CONV_T1_L32 * kExactShapes + 2: return F<ConvT1<false>, exact_shape_warps(2), exact_shape_rpw(2)>::run(a...);
+    case CONV_T1_L16 * kExactShapes + 0: return F<ConvT1<true>, exact_shape_warps(0), exact_shape_rpw(0)>::run(a...);
+    case CONV_T1_L16 * kExactShapes + 1: return F<ConvT1<true>, exact_shape_warps(1), exact_shape_rpw(1)>::run(a...);
+    case CONV_T1_L16 * kExactShapes + 2: return F<ConvT1<true>, exact_shape_warps(2), exact_shape_rpw(2)>::run(a...);
+    case CONV_GENERIC * kExactShapes + 1: return F<ConvGeneric, exact_shape_warps(1), exact_shape_rpw(1)>::run(a...);
+    case CONV_GENERIC * kExactShapes + 2: return F<ConvGeneric, exact_shape_warps(2), exact_shape_rpw(2)>::run(a...);
+    default: return F<ConvGeneric, exact_shape_warps(0), exact_shape_rpw(0)>::run(a...);
+  }
+}
+
+template <class Conv, int W, int RPW>
+struct Launch {
+  static cudaError_t run(const ExactParams* P, int grid, cudaStream_t stream) {
+    return launch_conv<Conv, W, RPW>(*P, grid, stream);
+  }
+};
+template <class Conv, int W, int RPW>
+struct MaxActive {
+  static int run(size_t smem) { return max_active<Conv, W, RPW>(smem); }
+};
+
 }  // namespace
 
-size_t exact_smem_bytes(int stages, int stage_bytes) {
-  return static_cast<size_t>(stages) * stage_bytes + kWarps * kDigitTileBytes +
+size_t exact_smem_bytes(int shape, int stages, int stage_bytes) {
+  return static_cast<size_t>(stages) * stage_bytes + exact_shape_warps(shape) * kDigitTileBytes +
          kDigits * kDigits * sizeof(unsigned long long) + 2 * kExactMaxStages * sizeof(uint64_t);
 }
 
-int exact_pick_stages(int stage_bytes) {
+int exact_pick_stages(int shape, int stage_bytes) {
   for (int st = kExactMaxStages; st >= 2; --st)
-    if (exact_smem_bytes(st, stage_bytes) <= 226 * 1024) return st;
+    if (exact_smem_bytes(shape, st, stage_bytes) <= 226 * 1024) return st;
   return 0;
 }
 
-cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream) {
-  switch (conv) {
-    case CONV_T1_L32: return launch_conv<ConvT1<false>>(P, grid, stream);
-    case CONV_T1_L16: return launch_conv<ConvT1<true>>(P, grid, stream);
-    default: return launch_conv<ConvGeneric>(P, grid, stream);
+bool exact_layout(ExactParams& P, int shape) {
+  if (shape < 0 || shape >= kExactShapes) return false;
+  const int tile = exact_tile_rows(shape);
+  int off = 0;
+  for (int j = 0; j < P.p; ++j) {
+    P.col_off[j] = off;
+    off += stage_col_bytes(P.col_bytes[j], tile);
   }
+  const int stages = exact_pick_stages(shape, off);
+  if (stages == 0) return false;
+  P.shape = shape;
+  P.stage_bytes = off;
+  P.stages = stages;
+  return true;
 }
 
-int exact_max_active_blocks(int conv, int stages, int stage_bytes) {
-  const size_t smem = exact_smem_bytes(stages, stage_bytes);
-  switch (conv) {
-    case CONV_T1_L32: return max_active<ConvT1<false>>(smem);
-    case CONV_T1_L16: return max_active<ConvT1<true>>(smem);
-    default: return max_active<ConvGeneric>(smem);
-  }
+cudaError_t launch_exact(const ExactParams& P, int conv, int max_grid, cudaStream_t stream) {
+  const int64_t tile = exact_tile_rows(P.shape);
+  const int64_t tiles = (P.nmain + tile - 1) / tile;
+  const int grid = static_cast<int>(std::min<int64_t>(std::max(max_grid, 1), std::max<int64_t>(tiles, 1)));
+  return dispatch<Launch>(conv, P.shape, &P, grid, stream);
+}
+
+int exact_max_active_blocks(int conv, int shape, int stages, int stage_bytes) {
+  return dispatch<MaxActive>(conv, shape, exact_smem_bytes(shape, stages, stage_bytes));
 }
 
 }  // namespace ss

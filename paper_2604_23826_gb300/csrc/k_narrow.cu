@@ -380,16 +380,25 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         if (++se == kNStages) se = 0;
         const uint32_t taddr =
             tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * 128);
+        // 64 columns per round trip: four loads in flight, one wait
 #pragma unroll
-        for (int c0 = 0; c0 < NB; c0 += 16) {
-          float v[16];
-          tmem_ld16(taddr + c0, v);
-          if (X4) {  // columns 16 g .. 16 g + 7: h of columns 8 g + i; the next 8: their l
+        for (int c0 = 0; c0 < NB; c0 += 64) {
+          uint32_t v[4][16];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[c0 / 2 + i] += v[i] + v[8 + i];
-          } else {
+          for (int b = 0; b < 4; ++b) tmem_ld16_issue(taddr + c0 + 16 * b, v[b]);
+          tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+          for (int b = 0; b < 4; ++b) tmem_hold16(v[b]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int cb = c0 + 16 * b;
+            if (X4) {  // columns 16 g .. 16 g + 7: h of columns 8 g + i; the next 8: their l
+#pragma unroll
+              for (int i = 0; i < 8; ++i) acc[cb / 2 + i] += __uint_as_float(v[b][i]) + __uint_as_float(v[b][8 + i]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) acc[cb + i] += __uint_as_float(v[b][i]);
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

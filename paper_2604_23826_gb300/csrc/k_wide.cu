@@ -76,7 +76,6 @@ using tc05::pack_bf16x2;
 using tc05::bf_lo;
 using tc05::bf_hi;
 using tc05::two_sum;
-using tc05::tmem_ld16;
 using tc05::fp32_piece;
 
 template <bool X4>
@@ -413,12 +412,20 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_kernel(const __grid_constan
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * kWBlk);
+      // 32 columns per round trip: two loads in flight, one wait
 #pragma unroll
-      for (int c0 = 0; c0 < kWBlk; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + c0, v);
+      for (int c0 = 0; c0 < kWBlk; c0 += 32) {
+        uint32_t v[2][16];
+        tc05::tmem_ld16_issue(taddr + c0, v[0]);
+        tc05::tmem_ld16_issue(taddr + c0 + 16, v[1]);
+        tc05::tmem_wait_ld();
+        tc05::tmem_hold16(v[0]);
+        tc05::tmem_hold16(v[1]);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] += v[i];
+        for (int i = 0; i < 16; ++i) {
+          acc[c0 + i] += __uint_as_float(v[0][i]);
+          acc[c0 + 16 + i] += __uint_as_float(v[1][i]);
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();

@@ -43,6 +43,7 @@ struct ExactParams {
   int8_t pc1[kDigitPairs], pb1[kDigitPairs], ps1[kDigitPairs];
   int32_t p;
   int32_t direct;       // 1: some column is not 16-byte aligned -- consumers read global memory directly
+  int32_t shape;        // launch shape (0 .. kExactShapes - 1)
   int32_t stages;       // pipeline depth (2..kExactMaxStages)
   int32_t stage_bytes;  // bytes of one stage (multiple of 128)
   int64_t nrows;        // rows of this call
@@ -54,18 +55,25 @@ struct ExactParams {
   unsigned int* status;          // ctx sticky device status bits
 };
 
-// Rows of one pipeline stage of the EXACT pass.
-constexpr int kExactWarps = 15;                 // consumer warps; +1 producer warp
-constexpr int kExactThreads = (kExactWarps + 1) * 32;
-constexpr int kExactTile = kExactWarps * 64;    // 960 rows per stage, 64 per consumer warp
-constexpr int kExactMaxStages = 3;
-// Bytes one column of `elem_bytes`-byte values takes in a pipeline stage (128-byte granules).
-__host__ __device__ constexpr int stage_col_bytes(int elem_bytes) { return ((kExactTile * elem_bytes + 127) / 128) * 128; }
-size_t exact_smem_bytes(int stages, int stage_bytes);
+// Launch shapes of the EXACT pass: consumer warps (plus one producer warp) and rows each
+// consumer takes per stage (a multiple of 32).  One block per SM; the register budget falls
+// with the thread count (128, 96 and 80 per thread for 16, 20 and 24 warps).
+constexpr int kExactShapes = 3;
+__host__ __device__ constexpr int exact_shape_warps(int shape) { return shape == 0 ? 15 : shape == 1 ? 19 : 23; }
+__host__ __device__ constexpr int exact_shape_rpw(int shape) { return shape == 0 ? 64 : 32; }
+constexpr int kExactMaxStages = 6;
+__host__ __device__ constexpr int exact_tile_rows(int shape) { return exact_shape_warps(shape) * exact_shape_rpw(shape); }
+// Bytes one column of `elem_bytes`-byte values takes in a stage of `tile` rows (128-byte granules).
+__host__ __device__ constexpr int stage_col_bytes(int elem_bytes, int tile) { return ((tile * elem_bytes + 127) / 128) * 128; }
+size_t exact_smem_bytes(int shape, int stages, int stage_bytes);
 // Deepest pipeline (2..kExactMaxStages stages) whose shared memory fits one block, or 0.
-int exact_pick_stages(int stage_bytes);
-cudaError_t launch_exact(const ExactParams& P, int conv, int grid, cudaStream_t stream);
-int exact_max_active_blocks(int conv, int stages, int stage_bytes);
+int exact_pick_stages(int shape, int stage_bytes);
+// Stage layout of P's columns for a shape: col_off, stage_bytes, stages, shape (needs p and
+// col_bytes); false when the shape does not fit.
+bool exact_layout(ExactParams& P, int shape);
+// Launch with at most max_grid blocks (fewer when the rows have fewer stages).
+cudaError_t launch_exact(const ExactParams& P, int conv, int max_grid, cudaStream_t stream);
+int exact_max_active_blocks(int conv, int shape, int stages, int stage_bytes);
 
 // ---------------------------------------------------------------------------
 // FP64 CUDA-core passes (raw or shifted), fixed-order merge of block slots.

@@ -112,6 +112,53 @@ def test_exact_grid_chunk_and_repeat_invariance():
     _check_exact(ref, O.stats_table1(5, n))
 
 
+@pytest.mark.parametrize("layout", [G.STATS_T1_L32, G.STATS_T1_L16])
+@pytest.mark.parametrize("n", [17, 607, 608, 737, 100_003, 1_000_003])
+def test_exact_launch_shapes_agree_with_oracle(layout, n):
+    """Every launch shape of the exact pass (warps x rows per stage) against the oracle, ragged
+    sizes around the shapes' stage lengths (608, 736, 960 rows): bit-identical integer results."""
+    cols = G.gen_table1(seed=11, nrows=n, layout=layout)
+    st = O.stats_table1(11, n)
+    raws = []
+    for shape in (0, 1, 2):
+        with _ctx(layout) as ctx:
+            G.stats_set_exact_shape(ctx, shape)
+            G.stats_accumulate(ctx, cols, n)
+            raws.append(G.stats_raw(ctx))
+        _check_exact(raws[-1], st)
+    for r in raws[1:]:
+        assert r.S_exact == raws[0].S_exact and np.array_equal(r.S, raws[0].S) and np.array_equal(r.s, raws[0].s)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_exact_launch_shapes_generic_and_unaligned(shape):
+    """The generic converter in every shape, on aligned and unaligned columns (plain loads)."""
+    rng = np.random.default_rng(13)
+    n = 90_001
+    vals = [rng.integers(-30000, 30000, n + 1, dtype=np.int16), rng.integers(-2**20, 2**20, n + 1, dtype=np.int32),
+            rng.integers(-2**30, 2**30, n + 1, dtype=np.int64), (rng.standard_normal(n + 1) * 3.0)]
+    cfg = G.Config([G.STATS_I16, G.STATS_I32, G.STATS_I64, G.STATS_F64], G.STATS_EXACT, [0, 0, 0, 0],
+                   [-30000, -2**20, -2**30, -64.0], [30000, 2**20, 2**30, 64.0])
+    whole = [torch.from_numpy(x).cuda() for x in vals]
+    aligned = [torch.from_numpy(np.ascontiguousarray(x[1:])).cuda() for x in vals]
+    unaligned = [d[1:] for d in whole]  # 2, 4 or 8 bytes past a 16-byte boundary
+    st = O.stats_columns([v[1:].astype(np.int64) if v.dtype != np.float64 else v[1:] for v in vals])
+    for cols in (aligned, unaligned):
+        res = []
+        for sh in (0, shape):
+            with G.stats_init(cfg) as ctx:
+                G.stats_set_exact_shape(ctx, sh)
+                G.stats_accumulate(ctx, cols, n)
+                res.append(G.stats_raw(ctx))
+        assert res[0].S_exact == res[1].S_exact and np.array_equal(res[0].S, res[1].S)
+        for j in range(3):
+            for k in range(j, 3):
+                assert res[1].S_exact[j][k] == st.S[j][k]
+    with G.stats_init(cfg) as ctx:
+        with pytest.raises(G.StatsError):
+            G.stats_set_exact_shape(ctx, 3)
+
+
 def test_exact_merge_export_import():
     """merge(stats(X1), stats(X2)) = stats(X1 u X2); an exported image re-imports unchanged."""
     n1, n2 = 123_456, 654_321
