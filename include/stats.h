@@ -73,7 +73,11 @@ typedef enum { STATS_I16 = 0, STATS_I32 = 1, STATS_I64 = 2, STATS_F32 = 3, STATS
  *   STATS_FP64         the plain FP64 CUDA-core kernel with raw moments, as in the
  *                      paper (covariance = (S - s s^T / n) / (n - 1) in FP64); a
  *                      row-parallel kernel for p <= 12, a tiled one above.
- *   STATS_FP64_SHIFTED FP64 CUDA cores on x - c, c = the first row accumulated.
+ *   STATS_FP64_SHIFTED FP64 CUDA cores on x - c, c = the mean of the first rows accumulated
+ *                      (the first 64 rows of the first call, or all of them if fewer; for
+ *                      FP32 data in the BF16 and FP32 modes rounded to FP32).  A pivot near the
+ *                      mean keeps the shifted cross products small, so rounding in their
+ *                      accumulation does not survive the centering.
  *   STATS_BF16X3       FP32 data: x - c split into bf16 h + l; S ~ H^T H + H^T L + L^T H
  *                      on tensor cores (each 16-row block a fresh FP32 chain, added in
  *                      round-to-nearest FP32, then double-double); for p <= 64 plus the
@@ -180,7 +184,7 @@ stats_status stats_accumulate_batched(stats_ctx* const* ctxs, int32_t ntables, c
  * ("Data Representation and Sufficient Statistics").  Exact for STATS_EXACT;
  * STATS_FP64 adds in double-double.  The shifted modes (STATS_FP64_SHIFTED,
  * STATS_BF16X3, STATS_BF16X4, STATS_FP32) hold moments about each ctx's own pivot
- * (its first row): src's are re-expressed about dst's pivot, in double-double,
+ * (the mean of its first rows): src's are re-expressed about dst's pivot, in double-double,
  *   sum (x - c_d) = s'_src + n_src d,
  *   sum (x - c_d)(x - c_d)^T = S'_src + d s'_src^T + s'_src d^T + n_src d d^T,
  * with d = c_src - c_dst; an empty dst takes src's pivot.  Enqueued on dst's last

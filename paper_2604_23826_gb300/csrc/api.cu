@@ -644,7 +644,7 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
     for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
     S.p = c->p;
     S.shift = c->d_fshift;
-    CK(c, launch_split_shift(S, c->d_shift, st));
+    CK(c, launch_split_shift(S, nrows, c->d_shift, st));
     c->shift_set = true;
   }
   WideParams W{};
@@ -710,7 +710,7 @@ stats_status run_narrow(stats_ctx* c, const void* const* dcols, int64_t nrows, c
     for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
     S.p = c->p;
     S.shift = c->d_fshift;
-    CK(c, launch_split_shift(S, c->d_shift, st));
+    CK(c, launch_split_shift(S, nrows, c->d_shift, st));
     c->shift_set = true;
   }
   const int grid = std::max(1, c->sms);
@@ -872,7 +872,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     S.p = c->p;
     S.shift = c->d_fshift;
     if (!c->shift_set) {
-      CK(c, launch_split_shift(S, c->d_shift, st));
+      CK(c, launch_split_shift(S, nrows, c->d_shift, st));
       c->shift_set = true;
     }
     const int T = split_tile(c->p);
@@ -913,7 +913,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     C.p = c->p;
     if (c->mode != STATS_FP64) {
       if (!c->shift_set) {
-        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, c->d_shift, st));
+        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, nrows, c->d_shift, st));
         c->shift_set = true;
       }
       C.shift = c->d_shift;
@@ -953,7 +953,7 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     P.nrows = nrows;
     if (c->mode == STATS_FP64_SHIFTED) {
       if (!c->shift_set) {
-        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, c->d_shift, st));
+        CK(c, launch_set_shift(dcols, c->dtypes.data(), c->p, nrows, c->d_shift, st));
         c->shift_set = true;
       }
       P.shift = c->d_shift;

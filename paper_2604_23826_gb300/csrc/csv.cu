@@ -14,8 +14,10 @@
 //                      the stores of a warp are contiguous).
 // Number conversion is exact.  A real field is M * 10^E with M < 10^19 (the significant
 // digits as an integer, trailing zeros moved into E) and -38 <= E <= 19.  For E >= 0 the product M * 10^E is formed in
-// 128-bit integers; for E < 0 the quotient M * 2^s / 10^-E is found by binary long
-// division (a 64-bit quotient and a sticky remainder bit).  Either way the exact value is
+// 128-bit integers; for E < 0 the quotient M * 2^s / 10^-E (a 64-bit quotient and a sticky
+// remainder bit) comes, for -E <= 27, from one division by the normalised 5^-E with its
+// precomputed reciprocal (exact quotient and remainder), and below that from binary long
+// division.  Either way the exact value is
 // a 64-bit integer q plus a sticky fraction times a power of two, rounded once to
 // nearest, ties to even, to the 53 (FP64) or 24 (FP32) bits of the column type, and
 // assembled bit by bit.

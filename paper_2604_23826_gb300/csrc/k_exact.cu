@@ -10,10 +10,12 @@
 // (every digit |d| <= 255 is exact in f16) and FP32 accumulators.  Each product
 // is below 2^16 and a warp flushes its accumulators every 256 of its rows, so
 // every partial sum is an integer below 2^24 and FP32 never rounds.  Flushes go
-// by shared-memory integer atomics to an int64 block accumulator, then by global
-// integer atomics to a per-call int64 accumulator, which the last block to
-// finish adds to the context accumulator (integer addition: the result does not
-// depend on block order or on the shape of the launch).  S_jk = sum_{a,b} 256^(a+b) G[(j,a),(k,b)] is
+// to int32 partial sums (in registers, or for the shapes with more warps in a
+// per-warp shared-memory array), every 64 flushes by integer atomics to an int64
+// block accumulator in shared memory, then by global integer atomics to a
+// per-call int64 accumulator, which the last block to finish adds to the context
+// accumulator (integer addition: the result does not depend on block order or on
+// the shape of the launch).  S_jk = sum_{a,b} 256^(a+b) G[(j,a),(k,b)] is
 // recombined exactly by the finalize kernel.
 //
 // Pipeline: one producer warp moves each stage of every column from HBM to
@@ -37,6 +39,11 @@ namespace {
 
 constexpr int kDigitTileBytes = 32 * 64;  // 32 rows x 32 f16 digits
 constexpr int kFlushRows = 256;           // per warp: FP32 partial sums stay below 2^24
+constexpr int kI32Flushes = 64;           // int32 partial sums stay below 2^30
+// int32 partial sums of a warp held in shared memory (shapes with more than 15 consumer
+// warps, whose threads have too few registers for them): 24 per lane, lane-major
+constexpr int kI32Bytes = 24 * 32 * 4;
+__host__ __device__ constexpr bool i32_in_smem(int warps) { return warps > 15; }
 
 // ---- sources of raw column values: a shared-memory stage or global memory ----
 struct SmemSrc {
@@ -231,6 +238,9 @@ __host__ __device__ constexpr int tile_j(int e) { return e < 4 ? e : e - 2; }
 struct WarpAcc {
   float f[6][4];
 };
+struct WarpI32 {  // int32 partial sums in registers
+  int32_t i[6][4];
+};
 
 // One 32-row sub-step of a warp: stage the digits, two K=16 blocks of MMAs.
 __device__ __forceinline__ void warp_mma_32rows(uint32_t tile, int lane, const uint32_t (&w)[16], WarpAcc& acc) {
@@ -257,9 +267,31 @@ __device__ __forceinline__ void warp_mma_32rows(uint32_t tile, int lane, const u
   __syncwarp();
 }
 
-// FP32 accumulators (exact integers below 2^24) into the block's int64 accumulator in
-// shared memory: upper-triangle entries only, by integer atomics (order-independent).
-__device__ __forceinline__ void flush_to_block(WarpAcc& acc, unsigned long long* cta_acc, int lane) {
+// FP32 accumulators (exact integers below 2^24) into int32 partial sums: registers, or the
+// warp's shared array (each lane its own 24 words, so plain loads and stores suffice).
+__device__ __forceinline__ void flush_f32(WarpAcc& acc, WarpI32& ri) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      ri.i[e][r] += __float2int_rn(acc.f[e][r]);
+      acc.f[e][r] = 0.f;
+    }
+}
+__device__ __forceinline__ void flush_f32(WarpAcc& acc, int32_t* si, int lane) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      si[(4 * e + r) * 32 + lane] += __float2int_rn(acc.f[e][r]);
+      acc.f[e][r] = 0.f;
+    }
+}
+
+// int32 partial sums into the block's int64 accumulator in shared memory: upper-triangle
+// entries only, by integer atomics (order-independent); the partial sums restart at zero.
+template <class Get>
+__device__ __forceinline__ void flush_i32(Get&& get, unsigned long long* cta_acc, int lane) {
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int e = 0; e < 6; ++e)
@@ -267,10 +299,10 @@ __device__ __forceinline__ void flush_to_block(WarpAcc& acc, unsigned long long*
     for (int r = 0; r < 4; ++r) {
       const int row = 16 * tile_i(e) + g + ((r >> 1) << 3);
       const int col = 8 * tile_j(e) + 2 * t + (r & 1);
-      const int v = __float2int_rn(acc.f[e][r]);
+      int32_t& v = get(e, r);
       if (row <= col && v != 0)
         atomicAdd(&cta_acc[row * kDigits + col], static_cast<unsigned long long>(static_cast<long long>(v)));
-      acc.f[e][r] = 0.f;
+      v = 0;
     }
 }
 
@@ -280,7 +312,9 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __gri
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* stage_base = smem;
   uint8_t* dtiles = smem + P.stages * P.stage_bytes;
-  unsigned long long* cta_acc = reinterpret_cast<unsigned long long*>(dtiles + W * kDigitTileBytes);
+  int32_t* i32s = reinterpret_cast<int32_t*>(dtiles + W * kDigitTileBytes);  // i32_in_smem(W) only
+  unsigned long long* cta_acc =
+      reinterpret_cast<unsigned long long*>(dtiles + W * kDigitTileBytes + (i32_in_smem(W) ? W * kI32Bytes : 0));
   uint64_t* full = reinterpret_cast<uint64_t*>(cta_acc + kDigits * kDigits);
   uint64_t* empty = full + kExactMaxStages;
   __shared__ uint32_t s_bad;
@@ -339,12 +373,23 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __gri
   } else {
     // ---------------- consumers ----------------
     WarpAcc acc;
+    WarpI32 ri;
+    int32_t* si = i32s + warp * (kI32Bytes / 4);
 #pragma unroll
     for (int e = 0; e < 6; ++e)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc.f[e][r] = 0.f;
+      for (int r = 0; r < 4; ++r) {
+        acc.f[e][r] = 0.f;
+        if (i32_in_smem(W))
+          si[(4 * e + r) * 32 + lane] = 0;
+        else
+          ri.i[e][r] = 0;
+      }
+    auto get_i32 = [&](int e, int r) -> int32_t& {
+      return i32_in_smem(W) ? si[(4 * e + r) * 32 + lane] : ri.i[e][r];
+    };
     const uint32_t tile = smem_u32(dtiles + warp * kDigitTileBytes);
-    int sub = 0;
+    int sub = 0, flushes = 0;
     int s = 0;
     uint32_t ph = 0;  // phase parity of stage s's current use
     int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTile;
@@ -372,7 +417,14 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __gri
         warp_mma_32rows(tile, lane, w, acc);
         if (++sub == kFlushRows / 32) {
           sub = 0;
-          flush_to_block(acc, cta_acc, lane);
+          if (i32_in_smem(W))
+            flush_f32(acc, si, lane);
+          else
+            flush_f32(acc, ri);
+          if (++flushes == kI32Flushes) {
+            flushes = 0;
+            flush_i32(get_i32, cta_acc, lane);
+          }
         }
       }
       __syncwarp();
@@ -395,7 +447,11 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __gri
       }
       warp_mma_32rows(tile, lane, w, acc);
     }
-    flush_to_block(acc, cta_acc, lane);
+    if (i32_in_smem(W))
+      flush_f32(acc, si, lane);
+    else
+      flush_f32(acc, ri);
+    flush_i32(get_i32, cta_acc, lane);
   }
   if (bad) atomicOr(&s_bad, DEV_ERANGE);
   if (failed) atomicOr(&s_bad, DEV_ETIMEOUT);
@@ -481,7 +537,8 @@ struct MaxActive {
 }  // namespace
 
 size_t exact_smem_bytes(int shape, int stages, int stage_bytes) {
-  return static_cast<size_t>(stages) * stage_bytes + exact_shape_warps(shape) * kDigitTileBytes +
+  const int W = exact_shape_warps(shape);
+  return static_cast<size_t>(stages) * stage_bytes + W * kDigitTileBytes + (i32_in_smem(W) ? W * kI32Bytes : 0) +
          kDigits * kDigits * sizeof(unsigned long long) + 2 * kExactMaxStages * sizeof(uint64_t);
 }
 

@@ -124,10 +124,15 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_rows_kernel(const __grid_con
   }
 }
 
-// shift = the first row of the columns (only called with nrows >= 1)
+// shift = the mean of the first min(nrows, kPivotRows) rows of the columns (nrows >= 1)
 __global__ void set_shift_kernel(Fp64Params P) {
   const int j = threadIdx.x;
-  if (j < P.p) const_cast<double*>(P.shift)[j] = load_d(P.cols[j], P.dtype[j], 0);
+  const int k = static_cast<int>(min(static_cast<int64_t>(kPivotRows), P.nrows));
+  if (j < P.p) {
+    double sum = 0.0;
+    for (int i = 0; i < k; ++i) sum += load_d(P.cols[j], P.dtype[j], i);
+    const_cast<double*>(P.shift)[j] = sum / k;
+  }
 }
 
 }  // namespace
@@ -244,9 +249,10 @@ cudaError_t launch_merge_dd(double* dst_hi, double* dst_lo, const double* src_hi
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, double* shift,
+cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, int64_t rows, double* shift,
                              cudaStream_t stream) {
   Fp64Params P{};
+  P.nrows = rows;
   for (int j = 0; j < p && j < 256; ++j) {
     P.cols[j] = cols[j];
     P.dtype[j] = dtypes[j];

@@ -2,8 +2,8 @@
 // tensor cores, register-fragment form of the bf16 split (BF16x3 / BF16x4):
 // arxiv 2604.23826, "Data Representation and Sufficient Statistics" (column sums
 // and X^T X in one streaming pass, partials over row ranges combined), with the
-// shift of "Numerical Considerations" (r = x - c, c = the table's first row, so
-// that X^T X and n mu mu^T are never formed separately).
+// shift of "Numerical Considerations" (r = x - c, c = the mean of the table's first
+// rows, so that X^T X and n mu mu^T are never formed separately).
 //
 // Each value becomes r = h + l, h = bf16(r), l = bf16(r - h), and
 //   S' = sum r r^T  ~  L^T H + H^T L + H^T H + diag(L^T L)   (BF16x3)
@@ -12,14 +12,19 @@
 // does not average out, so BF16x3 adds it from the CUDA cores (an FFMA per value);
 // the off-diagonal terms are sums of products of rounding residuals and cancel.
 //
-// Data path.  The launch's tables are cut into 32 KB stages (8192 / P rows x P
-// columns); the stages of all tables, in order, are dealt round-robin to the
-// persistent CTAs (CTA b takes stages b, b + G, b + 2G, ...), so that at any
-// moment the CTAs read neighbouring row ranges of every column.  In a CTA a
-// producer warp streams its stages into a four-deep shared-memory ring with
-// one bulk copy (cp.async.bulk, mbarrier completion) per column; columns sit
-// RS + 16 floats apart, so that the consumers' 128-bit loads are free of bank
-// conflicts.  Seven consumer warps take the 16-row K blocks in turn.  Lane
+// Data path.  The launch's tables are cut into stages of RS rows x P columns
+// (P = 8, 16: 16384 / P rows, 64 KB; P = 32, 64: 240 rows); the stages of all
+// tables, in order, are dealt in chunks of consecutive stages round-robin to the
+// persistent CTAs (CTA b takes chunks b, b + G, ...; the chunk length comes from
+// the call's size and the batch tuning), so that neighbouring CTAs read
+// neighbouring row ranges of a large table and a small table stays in one CTA.
+// In a CTA a producer warp streams its stages into a shared-memory ring (3 stages
+// for P = 8, 16 and 64; 6 for P = 32): a table whose columns sit one 16-byte
+// multiple apart, with P >= 32, takes one 2D tensor copy per stage (zeros past p);
+// otherwise one bulk copy (cp.async.bulk, mbarrier completion) per column (4-8 KB
+// for P <= 16), and columns sit RS + 16 floats apart, so that the consumers'
+// 128-bit loads are free of bank conflicts.  Seven consumer warps take the 16-row
+// K blocks in turn.  Lane
 // (g, t) reads rows 4t..4t+3 of columns g + 8m with one 128-bit load per m;
 // those four rows fill the k slots (2t, 2t+1, 2t+8, 2t+9) of both the A
 // fragment (m16n8k16, A = X^T: rows = columns of X) and the B fragment
@@ -607,10 +612,14 @@ cudaError_t launch_p(const Gram32Launch& L, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// pivot c_j = the mean of the table's first kPivotRows rows (or all, if fewer), rounded to FP32
 __global__ void gram32_shift_kernel(const Gram32Table* __restrict__ tabs, const int* __restrict__ which) {
   const Gram32Table& T = tabs[which[blockIdx.x]];
+  const int k = static_cast<int>(min(static_cast<int64_t>(kPivotRows), T.nrows));
   for (int j = threadIdx.x; j < T.p; j += blockDim.x) {
-    const float v = T.cols[j][0];
+    double sum = 0.0;
+    for (int i = 0; i < k; ++i) sum += static_cast<double>(T.cols[j][i]);
+    const float v = static_cast<float>(sum / k);
     const_cast<float*>(T.shift)[j] = v;
     T.shift_d[j] = static_cast<double>(v);
   }

@@ -1,7 +1,7 @@
 // k_narrow.cu -- sufficient statistics of FP32 tables of 33 to 64 columns on the tcgen05
 // tensor cores: arxiv 2604.23826, "Data Representation and Sufficient Statistics" (column
 // sums and X^T X in one streaming pass, partials over row ranges combined), with the shift
-// of "Numerical Considerations" (r = x - c, c = the table's first row).
+// of "Numerical Considerations" (r = x - c, c = the mean of the table's first rows).
 //
 // The h and l halves of the split r = h + l (bf16 each) are stacked into one operand of
 // M = 128 rows, 8-column group by 8-column group: operand row 16 g + i is h of column
@@ -493,10 +493,14 @@ __global__ void __launch_bounds__(256) narrow_merge_kernel(const __grid_constant
   }
 }
 
+// pivot c_j = the mean of the table's first kPivotRows rows (or all, if fewer), rounded to FP32
 __global__ void narrow_shift_kernel(const NarrowTab* __restrict__ tabs, const int* __restrict__ which) {
   const NarrowTab& T = tabs[which[blockIdx.x]];
+  const int k = static_cast<int>(min(static_cast<int64_t>(kPivotRows), T.nrows));
   for (int j = threadIdx.x; j < T.p; j += blockDim.x) {
-    const float v = T.base[static_cast<int64_t>(j) * T.ld];
+    double sum = 0.0;
+    for (int i = 0; i < k; ++i) sum += static_cast<double>(T.base[static_cast<int64_t>(j) * T.ld + i]);
+    const float v = static_cast<float>(sum / k);
     T.shift[j] = v;
     T.shift_d[j] = static_cast<double>(v);
   }

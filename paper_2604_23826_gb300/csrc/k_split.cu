@@ -4,7 +4,7 @@
 // Statistics"; the shift against cancellation follows "Numerical
 // Considerations": X^T X and N mu mu^T must not be formed separately).
 //
-// Every value is shifted by a pivot c_j (the first row of the table), r = x - c,
+// Every value is shifted by a pivot c_j (the mean of the table's first rows), r = x - c,
 // and split r = h + l with h = bf16(r), l = bf16(r - h).  Then
 //   S' = sum_rows r r^T  ~  H^T H + H^T L + L^T H      (BF16x3)
 //                         + L^T L                      (BF16x4)
@@ -307,22 +307,27 @@ __global__ void __launch_bounds__(kThreads) split_batched_kernel(const SplitPara
   split_block<T, X4>(P.col_ptrs, P, u.y, P.ntiles * P.ksplit, sbuf, &s_last);
 }
 
-// shift = the first row of FP32 columns (called once, nrows >= 1)
-__global__ void split_shift_kernel(const __grid_constant__ SplitParams P, double* shift_d) {
+// pivot c_j = the mean of the first min(rows, kPivotRows) rows of FP32 columns, rounded to FP32
+// (called once, rows >= 1)
+__device__ void split_pivot(const SplitParams& P, int64_t rows, double* shift_d) {
+  const int k = static_cast<int>(min(static_cast<int64_t>(kPivotRows), rows));
   for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
-    const float v = (P.col_ptrs ? P.col_ptrs[j] : P.cols[j])[0];
+    const float* col = P.col_ptrs ? P.col_ptrs[j] : P.cols[j];
+    double sum = 0.0;
+    for (int i = 0; i < k; ++i) sum += static_cast<double>(col[i]);
+    const float v = static_cast<float>(sum / k);
     const_cast<float*>(P.shift)[j] = v;
     shift_d[j] = static_cast<double>(v);
   }
 }
 
+__global__ void split_shift_kernel(const __grid_constant__ SplitParams P, int64_t rows, double* shift_d) {
+  split_pivot(P, rows, shift_d);
+}
+
 __global__ void split_shift_batched_kernel(const SplitParams* __restrict__ tabs, const int* __restrict__ which) {
   const SplitParams& P = tabs[which[blockIdx.x]];
-  for (int j = threadIdx.x; j < P.p; j += blockDim.x) {
-    const float v = P.col_ptrs[j][0];
-    const_cast<float*>(P.shift)[j] = v;
-    P.shift_d[j] = static_cast<double>(v);
-  }
+  split_pivot(P, P.nrows, P.shift_d);
 }
 
 }  // namespace
@@ -369,8 +374,8 @@ cudaError_t launch_split_shift_batched(const SplitParams* tabs, const int* which
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_shift(const SplitParams& P, double* shift_d, cudaStream_t stream) {
-  split_shift_kernel<<<1, 256, 0, stream>>>(P, shift_d);
+cudaError_t launch_split_shift(const SplitParams& P, int64_t rows, double* shift_d, cudaStream_t stream) {
+  split_shift_kernel<<<1, 256, 0, stream>>>(P, rows, shift_d);
   return cudaGetLastError();
 }
 

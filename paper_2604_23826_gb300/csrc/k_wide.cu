@@ -2,7 +2,7 @@
 // tensor cores (tcgen05, accumulators in tensor memory): arxiv 2604.23826, "Data
 // Representation and Sufficient Statistics" (column sums and X^T X in one streaming
 // pass; partials over row ranges combined), with the shift of "Numerical
-// Considerations" (r = x - c, c = the table's first row).
+// Considerations" (r = x - c, c = the mean of the table's first rows).
 //
 // Work split.  The columns are cut into 128-column blocks; the output's upper block
 // triangle is a list of units (I, J), I <= J, each a 128 x 128 block of S'.  A diagonal

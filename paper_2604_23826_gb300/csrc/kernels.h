@@ -15,6 +15,7 @@ enum : uint32_t {
   DEV_EOVERFLOW = 4u  // an exact result does not fit its output type
 };
 
+constexpr int kPivotRows = 64;  // shifted modes: the pivot is the mean of a table's first rows
 constexpr int kMaxCols = 16;     // columns of the EXACT pass
 constexpr int kDigits = 32;      // digit slots of the EXACT pass (ones column included)
 constexpr int kDigitPairs = kDigits / 2;
@@ -93,7 +94,7 @@ struct Fp64Params {
 };
 cudaError_t launch_fp64(const Fp64Params& P, int grid, cudaStream_t stream);
 size_t fp64_slot_doubles(int grid);  // slots + ticket word, zeroed once at allocation
-cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, double* shift,
+cudaError_t launch_set_shift(const void* const* cols, const int32_t* dtypes, int p, int64_t rows, double* shift,
                              cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
@@ -121,7 +122,9 @@ struct SplitParams {
 size_t split_slot_floats(int grid);
 int split_tile(int p);  // T = 32 or 64
 cudaError_t launch_split(const SplitParams& P, int T, bool x4, int grid, cudaStream_t stream);
-cudaError_t launch_split_shift(const SplitParams& P, double* shift_d, cudaStream_t stream);
+// Pivot of a shifted context from its first call: the mean of its first min(rows, kPivotRows)
+// rows (FP32 data: rounded to FP32, so that x - c is exact wherever Sterbenz's lemma holds).
+cudaError_t launch_split_shift(const SplitParams& P, int64_t rows, double* shift_d, cudaStream_t stream);
 // pivots of tabs[which[i]] for i < count, one block per table (batched launches)
 cudaError_t launch_split_shift_batched(const SplitParams* tabs, const int* which, int count, cudaStream_t stream);
 // units[i] = (index into tabs, local block of that table); all tables share T and the mode
@@ -166,7 +169,7 @@ int gram32_width(int p);                 // P = 8, 16, 32 or 64
 size_t gram32_slot_floats(int P);        // floats of one warp / unit slot
 int gram32_rows_per_stage(int P);
 cudaError_t launch_gram32(const Gram32Launch& L, int P, bool x4, int grid, cudaStream_t st);
-// pivots (first rows) of tabs[which[i]], i < count
+// pivots (means of the first kPivotRows rows) of tabs[which[i]], i < count
 cudaError_t launch_gram32_shift(const Gram32Table* tabs, const int* which, int count, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -241,7 +244,7 @@ struct NarrowParams {
 };
 // CTA b takes units b, b + grid, ...; then one merge block per (row of S or column sums, table).
 cudaError_t launch_narrow(const NarrowParams& P, bool x4, int grid, cudaStream_t st);
-// Pivots (the first row) of tables which[0 .. count) of a device table list.
+// Pivots (the means of the first kPivotRows rows) of tables which[0 .. count) of a device table list.
 cudaError_t launch_narrow_shift(const NarrowTab* tabs, const int* which, int count, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
