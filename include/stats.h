@@ -320,6 +320,13 @@ stats_status stats_get_batch_tuning(int32_t width, int32_t mode, stats_batch_tun
  * Applies to later finalize calls on ctx.  Errors: EINVAL. */
 stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent_block);
 
+/* Kernel of STATS_BF16X3 / STATS_BF16X4 for tables of 129..256 FP32 columns stored as one
+ * [p, ld] block: 1 (default) = pairs of SMs, each CTA of a pair converting one 128-column block
+ * and the pair's 256 x 256 product formed by tcgen05 MMAs spanning both (the table is read
+ * once); 0 = one CTA per 128 x 128 output block (blocks shared by two outputs are read twice).
+ * Results agree to rounding.  Errors: EINVAL. */
+stats_status stats_set_wide_pairs(stats_ctx* ctx, int32_t pairs);
+
 /* Launch shape of the STATS_EXACT pass (-1 = the library's default for the ctx's converter):
  *   0  15 consumer warps, 64 rows each per stage (960-row stages)
  *   1  19 consumer warps, 32 rows each (608-row stages)

@@ -319,6 +319,14 @@ def stats_get_batch_tuning(width: int, mode: int) -> dict:
     return {f: getattr(v, f) for f, _ in _BatchTuning._fields_}
 
 
+def stats_set_wide_pairs(ctx: Ctx, pairs: int):
+    """129..256 FP32 columns in a [p, ld] block: 1 = the paired-CTA pass, 0 = one CTA per output block."""
+    L = load()
+    L.stats_set_wide_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    L.stats_set_wide_pairs.restype = ctypes.c_int
+    _check(L.stats_set_wide_pairs(ctx.handle, pairs), "stats_set_wide_pairs")
+
+
 def stats_set_exact_shape(ctx: Ctx, shape: int):
     """Launch shape of the STATS_EXACT pass (-1: default; 0, 1, 2: see stats.h)."""
     L = load()

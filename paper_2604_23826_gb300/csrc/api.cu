@@ -90,6 +90,7 @@ struct stats_ctx {
   int split_grid = 0;
   int flush_rows = 0;                   // 0: by table width
   int exact_shape = -1;                 // EXACT launch shape (-1: the converter's default)
+  int wide_pairs = 1;                   // 129..256 FP32 columns: the paired-CTA tcgen05 pass
   int64_t grid_wait_ns = 0;             // eigen-solver grid waits: limit (0: 2 s)
   int32_t grid_absent_block = -1;       // testing: a block of the eigen-solver that never arrives
   // the last 2D tensor map made for this ctx's FP32 columns (reused while the layout is the same)
@@ -680,6 +681,47 @@ stats_status run_wide(stats_ctx* c, const void* const* dcols, int64_t nrows, cud
   return STATS_OK;
 }
 
+// 129..256 columns of one [p, ld] block (tensor map current in c->tmap): the paired-CTA pass.
+stats_status run_wide2(stats_ctx* c, const void* const* dcols, int64_t nrows, cudaStream_t st) {
+  if (!c->shift_set) {
+    SplitParams S{};
+    for (int j = 0; j < c->p; ++j) S.cols[j] = static_cast<const float*>(dcols[j]);
+    S.p = c->p;
+    S.shift = c->d_fshift;
+    CK(c, launch_split_shift(S, nrows, c->d_shift, st));
+    c->shift_set = true;
+  }
+  const int grid = wide2_grid(c->sms);
+  const size_t pairs = static_cast<size_t>(grid) * kWide2SlotPairs;
+  if (!c->d_wide_slots || static_cast<size_t>(c->wide_grid_alloc) * kWideSlotPairs < pairs) {
+    if (c->d_wide_slots) CK(c, cudaFree(c->d_wide_slots));
+    c->d_wide_slots = nullptr;
+    CK(c, cudaMalloc(&c->d_wide_slots, pairs * 2 * sizeof(float)));
+    c->wide_grid_alloc = static_cast<int>((pairs + kWideSlotPairs - 1) / kWideSlotPairs);
+  }
+  if (!c->d_tmap) CK(c, cudaMalloc(&c->d_tmap, sizeof(CUtensorMap)));
+  CK(c, cudaMemcpyAsync(c->d_tmap, &c->tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  Wide2Params W{};
+  W.tmap = c->d_tmap;
+  W.base = static_cast<const float*>(dcols[0]);
+  W.ld = (static_cast<const char*>(dcols[1]) - static_cast<const char*>(dcols[0])) / 4;
+  W.shift = c->d_fshift;
+  W.slots = c->d_wide_slots;
+  W.acc_s = c->d_fs;
+  W.acc_s_lo = c->d_fs_lo;
+  W.acc_S = c->d_fS;
+  W.acc_S_lo = c->d_fS_lo;
+  W.acc_n = c->d_fn;
+  W.status = c->d_status;
+  W.nrows = nrows;
+  W.nfull = nrows / wide_chunk_rows();
+  W.p = c->p;
+  const int flush_rows = c->flush_rows > 0 ? c->flush_rows : 16384;
+  W.flush_stages = std::max(1, flush_rows / wide_rows_per_stage());
+  CK(c, launch_wide2(W, split_x4(c, nrows), grid, st));
+  return STATS_OK;
+}
+
 // The narrow-pass description of one table (its tensor map must be current in c->tmap).
 NarrowTab narrow_table(stats_ctx* c, const void* const* dcols, int64_t nrows) {
   NarrowTab T{};
@@ -864,7 +906,8 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     stats_status s = run_gram32(jobs, st);
     if (s != STATS_OK) return s;
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && wide_eligible(c, dcols, nrows)) {
-    stats_status s = run_wide(c, dcols, nrows, st);
+    stats_status s = (c->wide_pairs && c->p <= 2 * wide_block_cols() && c->sms >= 2) ? run_wide2(c, dcols, nrows, st)
+                                                                                      : run_wide(c, dcols, nrows, st);
     if (s != STATS_OK) return s;
   } else if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
     SplitParams S{};
@@ -2016,6 +2059,12 @@ stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent
   if (!ctx || wait_ns < 0 || wait_ns > int64_t(60) * 1000000000 || absent_block < -1) return STATS_EINVAL;
   ctx->grid_wait_ns = wait_ns;
   ctx->grid_absent_block = absent_block;
+  return STATS_OK;
+}
+
+stats_status stats_set_wide_pairs(stats_ctx* ctx, int32_t pairs) {
+  if (!ctx || (pairs != 0 && pairs != 1)) return STATS_EINVAL;
+  ctx->wide_pairs = pairs;
   return STATS_OK;
 }
 

@@ -124,14 +124,17 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_rows_kernel(const __grid_con
   }
 }
 
-// shift = the mean of the first min(nrows, kPivotRows) rows of the columns (nrows >= 1)
+// shift = the mean of the first min(nrows, kPivotRows) rows of the columns (nrows >= 1); for
+// FP32 columns rounded to FP32, so that x - c is exact wherever x and c are within a factor
+// of two of each other (and the FP32-core pass's rounding of x - c to FP32 is exact there)
 __global__ void set_shift_kernel(Fp64Params P) {
   const int j = threadIdx.x;
   const int k = static_cast<int>(min(static_cast<int64_t>(kPivotRows), P.nrows));
   if (j < P.p) {
     double sum = 0.0;
     for (int i = 0; i < k; ++i) sum += load_d(P.cols[j], P.dtype[j], i);
-    const_cast<double*>(P.shift)[j] = sum / k;
+    const double c = sum / k;
+    const_cast<double*>(P.shift)[j] = P.dtype[j] == F32 ? static_cast<double>(static_cast<float>(c)) : c;
   }
 }
 

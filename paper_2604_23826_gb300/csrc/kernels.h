@@ -207,6 +207,28 @@ int wide_rows_per_stage();
 int wide_chunk_rows();
 int wide_block_cols();
 cudaError_t launch_wide(const WideParams& P, bool x4, int grid, cudaStream_t st);
+// 129..256 columns on pairs of SMs (k_wide2.cu): cluster of two CTAs, CTA rank r converts
+// column block r, the pair's leader issues cta_group::2 MMAs of M = N = 256.
+constexpr int kWide2SlotPairs = 128 * 256 + 2 * 128;  // (hi, lo) pairs of a CTA's slot
+struct Wide2Params {
+  const void* tmap;          // 3D tensor map: dims (32, nrows / 32, p), box (32, 2, 128), 128-byte swizzle
+  const float* base;         // column 0; column j at base + j * ld
+  const float* shift;        // p pivots (device)
+  float* slots;              // grid * kWide2SlotPairs pairs of scratch
+  double* acc_s;             // ctx accumulators (shifted), double-double
+  double* acc_s_lo;
+  double* acc_S;
+  double* acc_S_lo;
+  long long* acc_n;
+  unsigned int* status;      // the ctx's device status word (DEV_* bits)
+  int64_t nrows;
+  int64_t ld;                // floats between consecutive columns (a multiple of 4)
+  int64_t nfull;             // whole 32-row chunks (nrows / 32); the rest is read with plain loads
+  int32_t p;
+  int32_t flush_stages;      // 64-row stages between FP32 -> (hi, lo) flushes
+};
+int wide2_grid(int sms);  // an even number of CTAs, at most sms
+cudaError_t launch_wide2(const Wide2Params& P, bool x4, int grid, cudaStream_t st);
 // 33..64 columns (k_narrow.cu): one 64-column block, h and l stacked into an M = 128 operand;
 // WideParams with a single unit (0, 0) of `grid` CTAs, tmap boxed (32, 2, 64).
 int narrow_cols();
