@@ -906,8 +906,8 @@ stats_status launch_pass(stats_ctx* c, const void* const* dcols, int64_t nrows, 
     stats_status s = run_gram32(jobs, st);
     if (s != STATS_OK) return s;
   } else if ((c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) && wide_eligible(c, dcols, nrows)) {
-    stats_status s = (c->wide_pairs && c->p <= 2 * wide_block_cols() && c->sms >= 2) ? run_wide2(c, dcols, nrows, st)
-                                                                                      : run_wide(c, dcols, nrows, st);
+    const bool pairs = c->wide_pairs && c->p > wide_block_cols() && c->p <= 2 * wide_block_cols() && c->sms >= 2;
+    stats_status s = pairs ? run_wide2(c, dcols, nrows, st) : run_wide(c, dcols, nrows, st);
     if (s != STATS_OK) return s;
   } else if (c->mode == STATS_BF16X3 || c->mode == STATS_BF16X4) {
     SplitParams S{};

@@ -60,7 +60,7 @@ constexpr int kPStages = 6;                      // 192 KB ring
 constexpr int kPThreads = 512;
 constexpr int kPConv = 4;                        // converter warps 4..7, four 8-column groups each
 constexpr int kPEpi = 8;                         // epilogue warps 8..15
-constexpr int kPRegsLow = 88, kPRegsEpi = 168;   // 2 x 128 x 88 + 2 x 128 x 168 = 65536
+constexpr int kPRegsLow = 104, kPRegsEpi = 152;  // 2 x 128 x 104 + 2 x 128 x 152 = 65536
 constexpr uint32_t kPLbo = 256, kPSbo = 2048;    // next K group (8 rows), next 8 operand rows
 constexpr int kPTmemCols = 512;                  // two 256-column accumulators
 constexpr int kPFold = 16;                       // stages of FP32 partial sums of l^2 per fold
@@ -294,52 +294,61 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
         }
         __syncwarp();
       }
+      // two groups at a time: both groups' FP32 in registers, then both converted (independent
+      // chains for the scheduler to interleave)
 #pragma unroll
-      for (int gi = 0; gi < 4; ++gi) {
-        const int g = 4 * cw + gi;
-        float4 x[2][2];
+      for (int g2 = 0; g2 < 4; g2 += 2) {
+        float4 x[2][2][2];
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
-          x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
-          x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+        for (int u = 0; u < 2; ++u) {
+          const int g = 4 * cw + g2 + u;
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
+            x[u][it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+            x[u][it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+          }
         }
-        __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
-        const float ncp = -s_piv[8 * g + sub];
-        const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+        __syncwarp();  // the groups' FP32 is in registers before their h and l overwrite it
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int j = (sub >> 2) ^ it;
-          const int row = kPChunk * j + 8 * qd;
-          float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
-                         __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
-                         __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
-                         __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
-          if (rows < kPRows) {
+        for (int u = 0; u < 2; ++u) {
+          const int gi = g2 + u, g = 4 * cw + gi;
+          const float ncp = -s_piv[8 * g + sub];
+          const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int j = (sub >> 2) ^ it;
+            const int row = kPChunk * j + 8 * qd;
+            float2 r[4] = {__fadd2_rn(make_float2(x[u][it][0].x, x[u][it][0].y), np),
+                           __fadd2_rn(make_float2(x[u][it][0].z, x[u][it][0].w), np),
+                           __fadd2_rn(make_float2(x[u][it][1].x, x[u][it][1].y), np),
+                           __fadd2_rn(make_float2(x[u][it][1].z, x[u][it][1].w), np)};
+            if (rows < kPRows) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (row + 2 * q >= rows) r[q].x = 0.f;
+                if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+              }
+            }
+            uint32_t h[4], l[4];
+            float2 e[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              if (row + 2 * q >= rows) r[q].x = 0.f;
-              if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+              h[q] = pack_bf16x2(r[q].x, r[q].y);
+              e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+              l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
             }
-          }
-          uint32_t h[4], l[4];
-          float2 e[4];
+            const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
+            two_sum(sh[gi], sl[gi], a.x + a.y);
+            two_sum(sh[gi], sl[gi], b.x + b.y);
+            if (!X4) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            h[q] = pack_bf16x2(r[q].x, r[q].y);
-            e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
-            l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
+              for (int q = 0; q < 4; ++q) pq[gi] = __ffma2_rn(e[q], e[q], pq[gi]);
+            }
+            uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
+            *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
           }
-          const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
-          two_sum(sh[gi], sl[gi], a.x + a.y);
-          two_sum(sh[gi], sl[gi], b.x + b.y);
-          if (!X4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pq[gi] = __ffma2_rn(e[q], e[q], pq[gi]);
-          }
-          uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
-          *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
