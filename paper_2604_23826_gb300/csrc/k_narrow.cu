@@ -29,12 +29,12 @@
 //               place, its h core matrices (first KB) and l core matrices (second KB), K group
 //               kk at + kk * 128, so a warp writes only what it read; column sums of r and
 //               (BF16x3) sum l^2;
-//   warp 1      MMA issuer: per 64-row stage a fresh chain of four K = 16 MMAs into one of
-//               two TMEM buffers and one commit (each tcgen05 instruction costs the issuing
-//               thread ~65 cycles, so a stage carries as few as possible);
+//   warp 1      MMA issuer: per 64-row stage four K = 16 MMAs and a commit that frees the
+//               stage; every two stages of a unit (128 rows) are one fresh chain in one of four
+//               TMEM buffers, committed to the epilogue at its end;
 //   warps 12-15 epilogue: each thread owns TMEM lane m, adds every chain into 64 FP32
 //               registers (round to nearest) and, every flush, into (hi, lo) pairs in the
-//               CTA's slot; on seeing a chain's commit it hands the stage back to the producer.
+//               CTA's slot, draining a TMEM buffer per chain.
 // Every wait is bounded: on expiry the CTA records STATS_ETIMEOUT and winds down.
 #include <algorithm>
 
@@ -58,7 +58,9 @@ constexpr int kNThreads = 512;
 constexpr int kNConv = 8;                         // converter warps 4 .. 11
 constexpr int kNRegsLow = 104, kNRegsEpi = 200;   // 3 x 104 + 200 = 4 x 128 per SMSP
 constexpr uint32_t kNLbo = 128, kNSbo = 1024;     // next K group, next 8 operand rows (h, l alternate)
-constexpr int kNTmemCols = 256;
+constexpr int kNBufs = 4;                         // accumulator buffers in tensor memory (128 columns each)
+constexpr int kNChain = 2;                        // stages per accumulation chain (128 rows) within a unit
+constexpr int kNTmemCols = 128 * kNBufs;
 constexpr int kNFold = 16;                        // stages of FP32 partial sums of l^2 per fold
 constexpr int kNSlotStride = 128;                 // pairs per slot row (the wide pass's slot layout)
 
@@ -81,7 +83,7 @@ __device__ __forceinline__ const NarrowTab& narrow_tab(const NarrowParams& P, in
 template <bool X4>
 __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_constant__ NarrowParams P) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t f_full[kNStages], c_full[kNStages], f_empty[kNStages], d_full[2], d_empty[2],
+  __shared__ __align__(8) uint64_t f_full[kNStages], c_full[kNStages], f_empty[kNStages], d_full[kNBufs], d_empty[kNBufs],
       fin;
   __shared__ uint32_t s_tmem;
   __shared__ volatile unsigned int s_dead;
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
       mbar_init(&c_full[s], kNConv);
       mbar_init(&f_empty[s], 1);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kNBufs; ++s) {
       mbar_init(&d_full[s], 1);
       mbar_init(&d_empty[s], 4);
     }
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
   if (warp < 12) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kNRegsLow));
 
   // Every role walks the same units (u = blockIdx.x, + gridDim.x, ...) and, in each, the same
-  // stages; the stage ring and the two TMEM buffers run on across units.
+  // stages; the stage ring and the TMEM buffers run on across units.
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     // (the whole warp runs the loop; one lane waits, one elected lane issues)
@@ -174,13 +176,16 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     bool live = true;
     for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
       const int nst = narrow_unit(P, u).nst;
-      for (int k = 0; k < nst; ++k, ++chains) {
-        // stage converted, and its TMEM buffer drained by the epilogue (two chains back)
-        const bool ok = __shfl_sync(0xffffffffu,
-                                    lane == 0 ? (wait_live(&c_full[s], ph, &s_dead) &&
-                                                 (chains < 2 || wait_live(&d_empty[bd], phd ^ 1u, &s_dead)))
-                                              : false,
-                                    0);
+      for (int k = 0; k < nst; ++k) {
+        // stage converted, and (at a chain's start) its TMEM buffer drained by the epilogue
+        const int in_chain = k % kNChain;
+        const bool last = in_chain == kNChain - 1 || k == nst - 1;
+        const bool ok = __shfl_sync(
+            0xffffffffu,
+            lane == 0 ? (wait_live(&c_full[s], ph, &s_dead) &&
+                         (in_chain != 0 || chains < kNBufs || wait_live(&d_empty[bd], phd ^ 1u, &s_dead)))
+                      : false,
+            0);
         if (!ok) {
           if (lane == 0) record_timeout(&s_dead, P.status);
           live = false;
@@ -189,22 +194,26 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t base = smem_u32(smem + static_cast<size_t>(s) * kNStageBytes);
         const uint32_t dt = tmem + static_cast<uint32_t>(bd * 128);
-        // one fresh chain per stage: K step ks = K groups 2 ks and 2 ks + 1; A = the stacked
-        // operand, B = the same (BF16x4) or its h rows.  The epilogue frees the stage once this
-        // commit has arrived.
+        // a fresh chain every kNChain stages of a unit: K step ks = K groups 2 ks and 2 ks + 1;
+        // A = the stacked operand, B = the same (BF16x4) or its h rows.  The stage is free once
+        // its MMAs have read it; the chain's buffer goes to the epilogue at its end.
         if (elect_one()) {
 #pragma unroll
           for (int ks = 0; ks < kNRows / 16; ++ks) {
             const uint64_t a = desc<kNLbo, kNSbo>(base + ks * 2 * kNLbo);
             const uint64_t b = X4 ? a : desc<kNLbo, 2 * kNSbo>(base + ks * 2 * kNLbo);
-            mma_bf16(dt, a, b, kIdesc, ks);
+            mma_bf16(dt, a, b, kIdesc, (in_chain != 0 || ks != 0) ? 1u : 0u);
           }
-          umma_commit(&d_full[bd]);
+          umma_commit(&f_empty[s]);
+          if (last) umma_commit(&d_full[bd]);
         }
         __syncwarp();
-        if (++bd == 2) {
-          bd = 0;
-          phd ^= 1u;
+        if (last) {
+          ++chains;
+          if (++bd == kNBufs) {
+            bd = 0;
+            phd ^= 1u;
+          }
         }
         if (++s == kNStages) {
           s = 0;
@@ -342,7 +351,7 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     float acc[kNCols];
 #pragma unroll
     for (int i = 0; i < kNCols; ++i) acc[i] = 0.f;
-    int bd = 0, se = 0;
+    int bd = 0;
     uint32_t phd = 0;
     bool live = true;
     for (int u = blockIdx.x; live && u < P.nunits; u += gridDim.x) {
@@ -367,7 +376,8 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         }
         fresh = false;
       };
-      for (int k = 0; k < U.nst; ++k) {
+      const int nchain = (U.nst + kNChain - 1) / kNChain;
+      for (int k = 0; k < nchain; ++k) {
         const bool ok = __all_sync(0xffffffffu, wait_live(&d_full[bd], phd, &s_dead));  // .sync.aligned loads follow
         if (!ok) {
           if (lane == 0) record_timeout(&s_dead, P.status);
@@ -375,9 +385,6 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the stage's MMAs have completed: its shared memory goes back to the producer
-        if (warp == 12 && lane == 0) mbar_arrive(&f_empty[se]);
-        if (++se == kNStages) se = 0;
         const uint32_t taddr =
             tmem + (static_cast<uint32_t>(32 * quarter) << 16) + static_cast<uint32_t>(bd * 128);
         // 64 columns per round trip: four loads in flight, one wait
@@ -404,11 +411,12 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&d_empty[bd]);
-        if (++bd == 2) {
+        if (++bd == kNBufs) {
           bd = 0;
           phd ^= 1u;
         }
-        if (++since >= P.flush_stages) {
+        since += kNChain;
+        if (since >= P.flush_stages) {
           since = 0;
           flush();
         }

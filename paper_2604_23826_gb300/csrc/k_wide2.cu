@@ -17,20 +17,25 @@
 // The whole 256 x 256 block is formed, half of it twice, so the tensor pipe does a third more
 // work than the upper triangle needs; it is not the bound.
 //
-// Each pair takes the 64-row stages q, q + pairs, ...; every stage is one fresh MMA chain.
+// Each pair takes the 64-row stages q, q + pairs, ...; every two stages (128 rows) are one
+// fresh MMA accumulation chain.
 // In a CTA (512 threads, four warpgroups):
 //   warp 0      producer: one 3D tensor copy of its block per stage (32 rows x 2 chunks x 128
 //               columns, 128-byte swizzle, zeros past p) into a ring of six 32 KB stages;
 //   warp 1      tensor memory (allocated by both CTAs together) and, in the leader, the MMA
 //               issuer: it waits until both CTAs have converted the stage and drained the
-//               accumulator buffer, issues the chain, and commits to the stage-free and
-//               chain-done barriers of both CTAs (multicast);
+//               accumulator buffer, issues the stage's MMAs, and commits to the stage-free and
+//               (at a chain's end) chain-done barriers of both CTAs (multicast);
+//   warps 2-3   in the peer, relays: its converter and epilogue warps arrive on local
+//               barriers, and one thread forwards each completed phase to the leader with a
+//               single cluster-scope arrive (a release at cluster scope stalls the arriving
+//               thread until its writes are visible to the pair);
 //   warps 4-7   converters: the stage's FP32 becomes, in place, the K-major core matrices of h
-//               and l (or 2l), four 8-column groups per warp; column sums of r and (BF16x3)
-//               sums of l^2; they report to the leader's barrier (a cluster-scope arrive);
+//               and l (or 2l), four 8-column groups per warp in turn; column sums of r and (BF16x3)
+//               sums of l^2;
 //   warps 8-15  epilogue: two warps per TMEM lane quarter, 128 columns each; every chain is
 //               added into FP32 registers (round to nearest), and every flush into (hi, lo)
-//               pairs in the CTA's slot; they report the drained buffer to the leader.
+//               pairs in the CTA's slot.
 // A second kernel adds the pairs' slots, in pair order, into the context's double-double
 // accumulators.  Every wait is bounded; on expiry the CTA records STATS_ETIMEOUT and winds
 // down; both CTAs always reach the final cluster barrier (no early exit).
@@ -60,10 +65,10 @@ constexpr int kPStages = 6;                      // 192 KB ring
 constexpr int kPThreads = 512;
 constexpr int kPConv = 4;                        // converter warps 4..7, four 8-column groups each
 constexpr int kPEpi = 8;                         // epilogue warps 8..15
-constexpr int kPRegsLow = 104, kPRegsEpi = 152;  // 2 x 128 x 104 + 2 x 128 x 152 = 65536
+constexpr int kPRegsLow = 96, kPRegsEpi = 160;   // 2 x 128 x 96 + 2 x 128 x 160 = 65536
 constexpr uint32_t kPLbo = 256, kPSbo = 2048;    // next K group (8 rows), next 8 operand rows
 constexpr int kPTmemCols = 512;                  // two 256-column accumulators
-constexpr int kPFold = 16;                       // stages of FP32 partial sums of l^2 per fold
+constexpr int kPChain = 2;                       // stages per MMA accumulation chain (128 rows)
 constexpr uint32_t kPIdesc = tc05::idesc_bf16(256, 256);
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -125,7 +130,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     wide2_kernel(const __grid_constant__ Wide2Params P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t f_full[kPStages], c_full[kPStages], f_empty[kPStages], d_full[2], d_empty[2],
-      fin;
+      fin, r_conv[kPStages], r_epi[2];
   __shared__ uint32_t s_tmem;
   __shared__ volatile unsigned int s_dead;
   __shared__ int s_rows[kPStages];
@@ -137,17 +142,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
   const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
   const int64_t nst = (P.nrows + kPRows - 1) / kPRows;
   const int64_t my = pair < nst ? (nst - 1 - pair) / npairs + 1 : 0;  // stages of this pair
+  const int64_t nchains = (my + kPChain - 1) / kPChain;                 // accumulation chains
   const int col0 = static_cast<int>(rank) * kPBlk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPStages; ++s) {
       mbar_init(&f_full[s], 1);
-      mbar_init(&c_full[s], 2 * kPConv);  // the leader's: both CTAs' converter warps
+      mbar_init(&c_full[s], kPConv + 1);  // the leader's: its converter warps + the peer's relay
       mbar_init(&f_empty[s], 1);
+      mbar_init(&r_conv[s], kPConv);      // the peer's: its converter warps, forwarded by the relay
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&d_full[b], 1);
-      mbar_init(&d_empty[b], 2 * kPEpi);  // the leader's: both CTAs' epilogue warps
+      mbar_init(&d_empty[b], kPEpi + 1);  // the leader's: its epilogue warps + the peer's relay
+      mbar_init(&r_epi[b], kPEpi);        // the peer's: its epilogue warps, forwarded by the relay
     }
     mbar_init(&fin, 1);
     s_dead = 0;
@@ -205,11 +213,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
       uint32_t ph = 0, phd = 0;
       bool live = true;
       for (int64_t k = 0; live && k < my; ++k) {
-        const bool ok = __shfl_sync(0xffffffffu,
-                                    lane == 0 ? (wait_cluster_live(&c_full[s], ph, &s_dead) &&
-                                                 (k < 2 || wait_cluster_live(&d_empty[bd], phd ^ 1u, &s_dead)))
-                                              : false,
-                                    0);
+        const int in_chain = static_cast<int>(k % kPChain);  // a chain starts on buffer bd at in_chain 0
+        const int64_t chain = k / kPChain;
+        const bool ok = __shfl_sync(
+            0xffffffffu,
+            lane == 0 ? (wait_cluster_live(&c_full[s], ph, &s_dead) &&
+                         (in_chain != 0 || chain < 2 || wait_cluster_live(&d_empty[bd], phd ^ 1u, &s_dead)))
+                      : false,
+            0);
         if (!ok) {
           if (lane == 0) record_timeout(&s_dead, P.status);
           live = false;
@@ -218,27 +229,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t base = smem_u32(smem + static_cast<size_t>(s) * kPStageBytes);
         const uint32_t dt = tmem + static_cast<uint32_t>(bd * 256);
+        const bool last = in_chain == kPChain - 1 || k == my - 1;
         if (tc05::elect_one()) {
-          // K step ks: K groups 2 ks, 2 ks + 1 of every 8-column group (h at +0, l at +128)
-          uint32_t acc = 0;
+          // K step ks: K groups 2 ks, 2 ks + 1 of every 8-column group (h at +0, l at +128).  The
+          // descriptors' address field is (address >> 4) in the low bits (no carry inside the
+          // 227 KB of shared memory), so the others are the stage's h descriptor plus an offset.
+          const uint64_t dh = pdesc(base), dl = dh + (128 >> 4);
+          constexpr uint64_t kStep = 512 >> 4;
+          uint32_t acc = in_chain != 0 ? 1u : 0u;
           if (X4) {
-#pragma unroll
-            for (int ks = 0; ks < kPRows / 16; ++ks, acc = 1)
-              mma2(dt, pdesc(base + ks * 512 + 128), pdesc(base + ks * 512 + 128), acc);  // L^T L
-#pragma unroll
-            for (int ks = 0; ks < kPRows / 16; ++ks)
-              mma2(dt, pdesc(base + ks * 512), pdesc(base + ks * 512 + 128), 1);  // H^T L
+#pragma unroll 1
+            for (int ks = 0; ks < kPRows / 16; ++ks, acc = 1) mma2(dt, dl + ks * kStep, dl + ks * kStep, acc);  // L^T L
+#pragma unroll 1
+            for (int ks = 0; ks < kPRows / 16; ++ks) mma2(dt, dh + ks * kStep, dl + ks * kStep, 1);  // H^T L
           }
-#pragma unroll
+#pragma unroll 1
           for (int ks = 0; ks < kPRows / 16; ++ks, acc = 1)
-            mma2(dt, pdesc(base + ks * 512), pdesc(base + ks * 512 + 128), acc);  // H^T L (BF16x3: 2l)
-#pragma unroll
-          for (int ks = 0; ks < kPRows / 16; ++ks) mma2(dt, pdesc(base + ks * 512), pdesc(base + ks * 512), 1);  // H^T H
-          commit2(&d_full[bd]);
+            mma2(dt, dh + ks * kStep, dl + ks * kStep, acc);  // H^T L (BF16x3: 2l)
+#pragma unroll 1
+          for (int ks = 0; ks < kPRows / 16; ++ks) mma2(dt, dh + ks * kStep, dh + ks * kStep, 1);  // H^T H
           commit2(&f_empty[s]);  // both CTAs' stage s is free once these MMAs have read it
+          if (last) commit2(&d_full[bd]);
         }
         __syncwarp();
-        if (++bd == 2) {
+        if (last && ++bd == 2) {
           bd = 0;
           phd ^= 1u;
         }
@@ -252,6 +266,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     }
     if (lane == 0) mbar_wait_bounded(&fin, 0);
     __syncwarp();
+  } else if (warp == 2 || warp == 3) {
+    // ---------------------------------------------------------------- relays (peer CTA)
+    // The peer's converter (warp 2) and epilogue (warp 3) warps arrive on local barriers; one
+    // thread forwards each completed phase to the leader with a single cluster-scope arrive,
+    // so the working warps never wait on a cluster-wide release themselves.
+    if (!leader && lane == 0) {
+      const bool conv = warp == 2;
+      uint64_t* local = conv ? r_conv : r_epi;
+      const uint32_t remote0 = cluster_addr(conv ? &c_full[0] : &d_empty[0], 0);
+      const int nb = conv ? kPStages : 2;
+      const int64_t count = conv ? my : nchains;
+      int b = 0;
+      uint32_t ph = 0;
+      for (int64_t k = 0; k < count; ++k) {
+        if (!tc05::wait_live(&local[b], ph, &s_dead)) {
+          record_timeout(&s_dead, P.status);
+          break;
+        }
+        arrive_cluster(remote0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
+        if (++b == nb) {
+          b = 0;
+          ph ^= 1u;
+        }
+      }
+    }
   } else if (warp >= 4 && warp < 4 + kPConv) {
     // ---------------------------------------------------------------- converters (in place)
     // Warp cw owns the 8-column groups 4 cw .. 4 cw + 3.  Group g's FP32 lines (columns 8g ..
@@ -261,15 +300,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     // j = (sub / 4) ^ it; every lane loads its pieces of the group before any lane stores.
     const int cw = warp - 4;
     const int sub = lane & 7, qd = lane >> 3;
-    const uint32_t lbar = cluster_addr(&c_full[0], 0);  // the leader's c_full[0]
-    float sh[4], sl[4], qh[4], ql[4];
-    float2 pq[4];
+    uint64_t* cbar = leader ? c_full : r_conv;  // the leader's own barrier, or the peer's relay
+    float sh[4], sl[4], qh[4], ql[4];  // (hi, lo) column sums of r and of l^2
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      sh[i] = sl[i] = qh[i] = ql[i] = 0.f;
-      pq[i] = make_float2(0.f, 0.f);
-    }
-    int since = 0;
+    for (int i = 0; i < 4; ++i) sh[i] = sl[i] = qh[i] = ql[i] = 0.f;
     const int64_t tail = P.nrows - P.nfull * kPChunk;  // rows after the last whole chunk (< 32)
     int s = 0;
     uint32_t ph = 0;
@@ -294,74 +328,59 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
         }
         __syncwarp();
       }
-      // two groups at a time: both groups' FP32 in registers, then both converted (independent
-      // chains for the scheduler to interleave)
 #pragma unroll
-      for (int g2 = 0; g2 < 4; g2 += 2) {
-        float4 x[2][2][2];
+      for (int gi = 0; gi < 4; ++gi) {
+        const int g = 4 * cw + gi;
+        float4 x[2][2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int g = 4 * cw + g2 + u;
-#pragma unroll
-          for (int it = 0; it < 2; ++it) {
-            const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
-            x[u][it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
-            x[u][it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
-          }
+        for (int it = 0; it < 2; ++it) {
+          const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
+          x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+          x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
         }
-        __syncwarp();  // the groups' FP32 is in registers before their h and l overwrite it
+        __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
+        const float ncp = -s_piv[8 * g + sub];
+        const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int gi = g2 + u, g = 4 * cw + gi;
-          const float ncp = -s_piv[8 * g + sub];
-          const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
-#pragma unroll
-          for (int it = 0; it < 2; ++it) {
-            const int j = (sub >> 2) ^ it;
-            const int row = kPChunk * j + 8 * qd;
-            float2 r[4] = {__fadd2_rn(make_float2(x[u][it][0].x, x[u][it][0].y), np),
-                           __fadd2_rn(make_float2(x[u][it][0].z, x[u][it][0].w), np),
-                           __fadd2_rn(make_float2(x[u][it][1].x, x[u][it][1].y), np),
-                           __fadd2_rn(make_float2(x[u][it][1].z, x[u][it][1].w), np)};
-            if (rows < kPRows) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                if (row + 2 * q >= rows) r[q].x = 0.f;
-                if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
-              }
-            }
-            uint32_t h[4], l[4];
-            float2 e[4];
+        for (int it = 0; it < 2; ++it) {
+          const int j = (sub >> 2) ^ it;
+          const int row = kPChunk * j + 8 * qd;
+          float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
+                         __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
+                         __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
+                         __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
+          if (rows < kPRows) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              h[q] = pack_bf16x2(r[q].x, r[q].y);
-              e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
-              l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
+              if (row + 2 * q >= rows) r[q].x = 0.f;
+              if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
             }
-            const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
-            two_sum(sh[gi], sl[gi], a.x + a.y);
-            two_sum(sh[gi], sl[gi], b.x + b.y);
-            if (!X4) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) pq[gi] = __ffma2_rn(e[q], e[q], pq[gi]);
-            }
-            uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
-            *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
           }
+          uint32_t h[4], l[4];
+          float2 e[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            h[q] = pack_bf16x2(r[q].x, r[q].y);
+            e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+            l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
+          }
+          const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
+          two_sum(sh[gi], sl[gi], a.x + a.y);
+          two_sum(sh[gi], sl[gi], b.x + b.y);
+          if (!X4) {  // this step's 8 squares in FP32, then into the (hi, lo) pair
+            float2 pq = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
+            two_sum(qh[gi], ql[gi], pq.x + pq.y);
+          }
+          uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
+          *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) arrive_cluster(lbar + static_cast<uint32_t>(s * sizeof(uint64_t)));
-      if (!X4 && ++since == kPFold) {
-        since = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          two_sum(qh[i], ql[i], pq[i].x + pq[i].y);
-          pq[i] = make_float2(0.f, 0.f);
-        }
-      }
+      if (lane == 0) mbar_arrive(&cbar[s]);
       if (++s == kPStages) {
         s = 0;
         ph ^= 1u;
@@ -369,7 +388,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      two_sum(qh[i], ql[i], pq[i].x + pq[i].y);
       // the 4 lanes of a column (sub equal) add their pairs (fixed order), lanes 0-7 write
 #pragma unroll
       for (int d = 8; d < 32; d <<= 1) {
@@ -394,7 +412,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. 32 quarter + 31
     const int half = (warp - 8) >> 2;             // accumulator columns 128 half .. 128 half + 127
     const int m = 32 * quarter + lane;            // this thread's row of the CTA's 128 x 256 half
-    const uint32_t lbar = cluster_addr(&d_empty[0], 0);  // the leader's d_empty[0]
+    uint64_t* ebar = leader ? d_empty : r_epi;  // the leader's own barrier, or the peer's relay
     float acc[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) acc[i] = 0.f;
@@ -402,14 +420,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
                    static_cast<size_t>(m) * 256 + 128 * half;
     bool fresh = true;
     int since = 0;
-    auto flush = [&]() {
+    auto flush = [&]() {  // four pairs at a time: the 128 sums leave little room
 #pragma unroll
-      for (int i0 = 0; i0 < 128; i0 += 8) {
-        float2 hl[8];
+      for (int i0 = 0; i0 < 128; i0 += 4) {
+        float2 hl[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(slot + i0 + k);
+        for (int k = 0; k < 4; ++k) hl[k] = fresh ? make_float2(0.f, 0.f) : __ldcg(slot + i0 + k);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 4; ++k) {
           two_sum(hl[k].x, hl[k].y, acc[i0 + k]);
           acc[i0 + k] = 0.f;
           __stcg(slot + i0 + k, hl[k]);
@@ -420,7 +438,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     };
     int bd = 0;
     uint32_t phd = 0;
-    for (int64_t k = 0; k < my; ++k) {
+    for (int64_t k = 0; k < nchains; ++k) {
       const bool ok = __all_sync(0xffffffffu, tc05::wait_live(&d_full[bd], phd, &s_dead));
       if (!ok) {
         if (lane == 0) record_timeout(&s_dead, P.status);
@@ -442,12 +460,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) arrive_cluster(lbar + static_cast<uint32_t>(bd * sizeof(uint64_t)));
+      if (lane == 0) mbar_arrive(&ebar[bd]);
       if (++bd == 2) {
         bd = 0;
         phd ^= 1u;
       }
-      if (++since >= P.flush_stages) {
+      since += kPChain;
+      if (since >= P.flush_stages) {
         since = 0;
         flush();
       }
