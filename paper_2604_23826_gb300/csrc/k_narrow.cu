@@ -59,7 +59,7 @@ constexpr int kNConv = 8;                         // converter warps 4 .. 11
 constexpr int kNRegsLow = 104, kNRegsEpi = 200;   // 3 x 104 + 200 = 4 x 128 per SMSP
 constexpr uint32_t kNLbo = 128, kNSbo = 1024;     // next K group, next 8 operand rows (h, l alternate)
 constexpr int kNBufs = 4;                         // accumulator buffers in tensor memory (128 columns each)
-constexpr int kNChain = 2;                        // stages per accumulation chain (128 rows) within a unit
+constexpr int kNChain = 4;                        // stages per accumulation chain (256 rows) within a unit
 constexpr int kNTmemCols = 128 * kNBufs;
 constexpr int kNFold = 16;                        // stages of FP32 partial sums of l^2 per fold
 constexpr int kNSlotStride = 128;                 // pairs per slot row (the wide pass's slot layout)
