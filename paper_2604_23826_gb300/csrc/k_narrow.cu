@@ -15,22 +15,23 @@
 // TMEM lane m accumulates its own row, so each epilogue thread keeps 64 FP32 sums (BF16x4
 // adds the h and l column of each d first); the merge kernel forms S from the slots.
 //
-// Work comes in units: a unit is a range of 64-row stages of one table (its own tensor map,
+// Work comes in units: a unit is a range of 128-row stages of one table (its own tensor map,
 // pivots and tail), and CTA b takes units b, b + grid, ....  A single-table call has one
 // unit of consecutive stages per CTA; a batched call deals the units of all its 33..64-column
 // tables, largest first.  Every unit is reduced into its own slot and the merge adds a
 // table's slots in row order, so the result depends on the units only.
 //
 // In a CTA (512 threads, four warpgroups; one CTA per SM):
-//   warp 0      producer: one 3D tensor copy per 64-row stage (32 rows x 2 chunks x 64
-//               columns, 128-byte swizzle, zero past p) into a ring of twelve 16 KB stages;
+//   warp 0      producer: one 3D tensor copy per 128-row stage (32 rows x 4 chunks x 64
+//               columns: 512 contiguous bytes per column, 128-byte swizzle, zero past p) into a
+//               ring of six 32 KB stages;
 //               rows past the last whole 32-row chunk are read by the converters;
-//   warps 4-11  converters, one 8-column group each: the group's 2 KB of FP32 becomes, in
-//               place, its h core matrices (first KB) and l core matrices (second KB), K group
+//   warps 4-11  converters, one 8-column group each: the group's 4 KB of FP32 becomes, in
+//               place, its h core matrices (first 2 KB) and l core matrices (second 2 KB), K group
 //               kk at + kk * 128, so a warp writes only what it read; column sums of r and
 //               (BF16x3) sum l^2;
-//   warp 1      MMA issuer: per 64-row stage four K = 16 MMAs and a commit that frees the
-//               stage; every two stages of a unit (128 rows) are one fresh chain in one of four
+//   warp 1      MMA issuer: per 128-row stage eight K = 16 MMAs and a commit that frees the
+//               stage; every two stages of a unit (256 rows) are one fresh chain in one of four
 //               TMEM buffers, committed to the epilogue at its end;
 //   warps 12-15 epilogue: each thread owns TMEM lane m, adds every chain into 64 FP32
 //               registers (round to nearest) and, every flush, into (hi, lo) pairs in the
@@ -50,16 +51,16 @@ using namespace tc05;
 
 constexpr int kNCols = 64;                        // columns of the block
 constexpr int kNChunk = 32;                       // rows per tensor-copy line
-constexpr int kNRows = 64;                        // rows per stage, and per MMA chain (4 K steps)
+constexpr int kNRows = 128;                       // rows per stage (8 K steps): 512 contiguous bytes per column
 constexpr int kNChunks = kNRows / kNChunk;
-constexpr int kNStageBytes = kNCols * kNRows * 4;  // 16 KB: FP32, then h (8 KB) and l (8 KB) in place
-constexpr int kNStages = 12;                      // 192 KB ring
+constexpr int kNStageBytes = kNCols * kNRows * 4;  // 32 KB: FP32, then h (16 KB) and l (16 KB) in place
+constexpr int kNStages = 6;                       // 192 KB ring
 constexpr int kNThreads = 512;
 constexpr int kNConv = 8;                         // converter warps 4 .. 11
 constexpr int kNRegsLow = 104, kNRegsEpi = 200;   // 3 x 104 + 200 = 4 x 128 per SMSP
-constexpr uint32_t kNLbo = 128, kNSbo = 1024;     // next K group, next 8 operand rows (h, l alternate)
+constexpr uint32_t kNLbo = 128, kNSbo = kNRows * 16;  // next K group, next 8 operand rows (h, l alternate)
 constexpr int kNBufs = 4;                         // accumulator buffers in tensor memory (128 columns each)
-constexpr int kNChain = 4;                        // stages per accumulation chain (256 rows) within a unit
+constexpr int kNChain = 2;                        // stages per accumulation chain (256 rows) within a unit
 constexpr int kNTmemCols = 128 * kNBufs;
 constexpr int kNFold = 16;                        // stages of FP32 partial sums of l^2 per fold
 constexpr int kNSlotStride = 128;                 // pairs per slot row (the wide pass's slot layout)
@@ -227,11 +228,11 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
     __syncwarp();
   } else if (warp >= 4 && warp < 4 + kNConv) {
     // ---------------------------------------------------------------- converters
-    // Warp cw owns columns 8 cw .. 8 cw + 7: their FP32 lines L = 2 c + chunk are the 2 KB at
-    // cw * 2048, where its h and l core matrices go.  Lane: column sub = lane % 8 of the group
-    // and, in step it (0, 1), K group kk = 4 j + lane / 8 of chunk j = (sub / 4) ^ it: a quarter
-    // warp reads 8 distinct swizzled 16-byte pieces and writes 8 distinct core-matrix rows (no
-    // bank conflicts).
+    // Warp cw owns columns 8 cw .. 8 cw + 7: their FP32 lines L = 4 c + chunk are the 4 KB at
+    // cw * 4096, where its h and l core matrices go.  Lane: column sub = lane % 8 of the group
+    // and, in step it (0 .. 3), K group kk = 4 j + lane / 8 of chunk j = (sub / 2) ^ it: a quarter
+    // warp reads 8 distinct swizzled 16-byte pieces (L mod 8 = 4 (sub mod 2) + j takes 8
+    // values) and writes 8 distinct core-matrix rows (no bank conflicts).
     const int cw = warp - 4;
     const int sub = lane & 7, qd = lane >> 3;
     const int c = 8 * cw + sub;
@@ -258,28 +259,29 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
         const int64_t st = U.st0 + k;
         const int rows = s_rows[s];
         uint8_t* base = smem + static_cast<size_t>(s) * kNStageBytes;
-        const int64_t jt = T.nfull - st * kNChunks;  // chunk of the stage holding the tail, if 0 or 1
-        if (tail > 0 && (jt == 0 || jt == 1)) {
+        const int64_t jt = T.nfull - st * kNChunks;  // chunk of the stage holding the tail, if in range
+        if (tail > 0 && jt >= 0 && jt < kNChunks) {
           if (lane < 8 && 8 * cw + lane < T.p) {
             const int cc = 8 * cw + lane;
-            const int L = 2 * cc + static_cast<int>(jt);
+            const int L = kNChunks * cc + static_cast<int>(jt);
             const float* src = T.base + static_cast<int64_t>(cc) * T.ld + T.nfull * kNChunk;
             for (int t = 0; t < static_cast<int>(tail); ++t)
               *reinterpret_cast<float*>(base + fp32_piece(L, t >> 2) + (t & 3) * 4) = src[t];
           }
           __syncwarp();
         }
-        float4 x[2][2];
+        static_assert(kNChunks == 4, "the lane mapping below covers four 32-row chunks per stage");
+        float4 x[kNChunks][2];
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int L = 2 * c + ((sub >> 2) ^ it);
+        for (int it = 0; it < kNChunks; ++it) {
+          const int L = kNChunks * c + ((sub >> 1) ^ it);
           x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
           x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
         }
         __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int j = (sub >> 2) ^ it;
+        for (int it = 0; it < kNChunks; ++it) {
+          const int j = (sub >> 1) ^ it;
           const int row = kNChunk * j + 8 * qd;
           float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
                          __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
