@@ -25,7 +25,7 @@ from typing import Dict, List, Optional, Sequence
 
 from . import binding as G
 
-NARROW_UNITS = (4, 6, 8, 12, 16, 24, 32, 48)
+NARROW_UNITS = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96)
 GRAM32_CHUNKING = ((32, 32), (8, 32), (16, 32), (64, 32), (32, 8), (32, 128), (16, 128), (64, 8))
 DEFAULT = {"narrow_units_per_cta": 12, "gram32_chunks_per_cta": 32, "gram32_min_chunk": 32}
 
