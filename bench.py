@@ -863,8 +863,9 @@ def run_wide(args, rank: int, world: int, local_rank: int):
               "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": m["GB_per_s"], "peak": peak, "unit": "GB/s", "frac": m["hbm_frac"],
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
-            "kernel": "wide_kernel (tcgen05, TMEM accumulators)" if main_mode.startswith("BF16") else
-            MODE_KERNEL[main_mode], "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
+            "kernel": (("wide2_kernel (tcgen05 cta_group::2, pairs of SMs, TMEM accumulators)" if 128 < p <= 256 else
+                        "wide_kernel (tcgen05, TMEM accumulators)") if main_mode.startswith("BF16") else
+                       MODE_KERNEL[main_mode]), "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
             "tensor_tflops_useful": flops_row * n / (m["ms"] / 1e3) / 1e12, "tensor_peak_tflops": tflops}
     t_ms = torch.tensor([m["ms"]], dtype=torch.float64, device=dev)
     if world > 1:
@@ -872,7 +873,8 @@ def run_wide(args, rank: int, world: int, local_rank: int):
         dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
     out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, wide FP32 table",
                      world * n / (t_ms.item() / 1e3), t_ms.item(), config, roof, clocks,
-                     2 * (args.steps if main_mode != "FP64S" else 1), {"modes": results})
+                     (3 if main_mode.startswith("BF16") else 2) * (args.steps if main_mode != "FP64S" else 1),
+                     {"modes": results})
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -930,8 +932,9 @@ def run_f32table(args, rank: int, world: int, local_rank: int):
               "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
-            "kernel": "gram32_kernel (register-fragment mma.sync bf16)" if p <= 64 and mode_name.startswith("BF16")
-            else MODE_KERNEL[mode_name], "kernel_ms": ms, "algorithmic_bytes": 4 * p * n}
+            "kernel": (("narrow_kernel (tcgen05, 33-64 columns)" if p > 32 and n >= (1 << 20) else
+                        "gram32_kernel (register-fragment mma.sync bf16)") if p <= 64 and mode_name.startswith("BF16")
+                       else MODE_KERNEL[mode_name]), "kernel_ms": ms, "algorithmic_bytes": 4 * p * n}
     extra = {"check_means_within_sqrt_n_sigma_units": float(np.max(np.abs(an.mean - mu32) / sd32)) * math.sqrt(n)}
     out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, one FP32 table",
                      world * n / (ms / 1e3), ms, config, roof, clocks,
