@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
           x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
         }
         __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
+        float2 t = make_float2(0.f, 0.f);  // two chunks' 16 values of this lane, a depth-4 tree
 #pragma unroll
         for (int it = 0; it < kNChunks; ++it) {
           const int j = (sub >> 1) ^ it;
@@ -302,9 +303,11 @@ __global__ void __launch_bounds__(kNThreads, 1) narrow_kernel(const __grid_const
             e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
             l[q] = pack_bf16x2(e[q].x, e[q].y);
           }
-          const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
-          two_sum(sh, sl, a.x + a.y);
-          two_sum(sh, sl, b.x + b.y);
+          t = __fadd2_rn(t, __fadd2_rn(__fadd2_rn(r[0], r[1]), __fadd2_rn(r[2], r[3])));
+          if (it & 1) {
+            two_sum(sh, sl, t.x + t.y);
+            t = make_float2(0.f, 0.f);
+          }
           if (!X4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);

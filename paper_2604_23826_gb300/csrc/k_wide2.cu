@@ -66,6 +66,7 @@ constexpr int kPThreads = 512;
 constexpr int kPConv = 4;                        // converter warps 4..7, four 8-column groups each
 constexpr int kPEpi = 8;                         // epilogue warps 8..15
 constexpr int kPRegsLow = 96, kPRegsEpi = 160;   // 2 x 128 x 96 + 2 x 128 x 160 = 65536
+constexpr int kPGroupsAtOnce = 2;  // 8-column groups a converter warp loads before converting
 constexpr uint32_t kPLbo = 256, kPSbo = 2048;    // next K group (8 rows), next 8 operand rows
 constexpr int kPTmemCols = 512;                  // two 256-column accumulators
 constexpr int kPChain = 2;                       // stages per MMA accumulation chain (128 rows)
@@ -329,53 +330,61 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
         __syncwarp();
       }
 #pragma unroll
-      for (int gi = 0; gi < 4; ++gi) {
-        const int g = 4 * cw + gi;
-        float4 x[2][2];
+      for (int g0 = 0; g0 < 4; g0 += kPGroupsAtOnce) {
+        // the FP32 of kPGroupsAtOnce groups in registers first: independent conversions to overlap
+        float4 x[kPGroupsAtOnce][2][2];
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
-          x[it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
-          x[it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+        for (int u = 0; u < kPGroupsAtOnce; ++u) {
+          const int g = 4 * cw + g0 + u;
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int L = 2 * (8 * g + sub) + ((sub >> 2) ^ it);
+            x[u][it][0] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd));
+            x[u][it][1] = *reinterpret_cast<const float4*>(base + fp32_piece(L, 2 * qd + 1));
+          }
         }
-        __syncwarp();  // the group's FP32 is in registers before its h and l overwrite it
-        const float ncp = -s_piv[8 * g + sub];
-        const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+        __syncwarp();  // the groups' FP32 is in registers before their h and l overwrite it
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int j = (sub >> 2) ^ it;
-          const int row = kPChunk * j + 8 * qd;
-          float2 r[4] = {__fadd2_rn(make_float2(x[it][0].x, x[it][0].y), np),
-                         __fadd2_rn(make_float2(x[it][0].z, x[it][0].w), np),
-                         __fadd2_rn(make_float2(x[it][1].x, x[it][1].y), np),
-                         __fadd2_rn(make_float2(x[it][1].z, x[it][1].w), np)};
-          if (rows < kPRows) {
+        for (int u = 0; u < kPGroupsAtOnce; ++u) {
+          const int gi = g0 + u, g = 4 * cw + gi;
+          const float ncp = -s_piv[8 * g + sub];
+          const float2 np = make_float2(ncp, ncp), m1 = make_float2(-1.f, -1.f);
+          // this lane's 16 values of the group in a depth-4 FP32 tree, its 16 squares of l in
+          // FP32, each then once into its (hi, lo) pair
+          float2 t = make_float2(0.f, 0.f), pq = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int j = (sub >> 2) ^ it;
+            const int row = kPChunk * j + 8 * qd;
+            float2 r[4] = {__fadd2_rn(make_float2(x[u][it][0].x, x[u][it][0].y), np),
+                           __fadd2_rn(make_float2(x[u][it][0].z, x[u][it][0].w), np),
+                           __fadd2_rn(make_float2(x[u][it][1].x, x[u][it][1].y), np),
+                           __fadd2_rn(make_float2(x[u][it][1].z, x[u][it][1].w), np)};
+            if (rows < kPRows) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (row + 2 * q >= rows) r[q].x = 0.f;
+                if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+              }
+            }
+            uint32_t h[4], l[4];
+            float2 e[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              if (row + 2 * q >= rows) r[q].x = 0.f;
-              if (row + 2 * q + 1 >= rows) r[q].y = 0.f;
+              h[q] = pack_bf16x2(r[q].x, r[q].y);
+              e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
+              l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
             }
-          }
-          uint32_t h[4], l[4];
-          float2 e[4];
+            t = __fadd2_rn(t, __fadd2_rn(__fadd2_rn(r[0], r[1]), __fadd2_rn(r[2], r[3])));
+            if (!X4)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            h[q] = pack_bf16x2(r[q].x, r[q].y);
-            e[q] = __ffma2_rn(make_float2(bf_lo(h[q]), bf_hi(h[q])), m1, r[q]);  // r - h, exact
-            l[q] = X4 ? pack_bf16x2(e[q].x, e[q].y) : pack_bf16x2(2.f * e[q].x, 2.f * e[q].y);
+              for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
+            uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
+            *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
           }
-          const float2 a = __fadd2_rn(r[0], r[1]), b = __fadd2_rn(r[2], r[3]);
-          two_sum(sh[gi], sl[gi], a.x + a.y);
-          two_sum(sh[gi], sl[gi], b.x + b.y);
-          if (!X4) {  // this step's 8 squares in FP32, then into the (hi, lo) pair
-            float2 pq = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pq = __ffma2_rn(e[q], e[q], pq);
-            two_sum(qh[gi], ql[gi], pq.x + pq.y);
-          }
-          uint8_t* cm = base + g * 2048 + (4 * j + qd) * 256 + sub * 16;
-          *reinterpret_cast<uint4*>(cm) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(cm + 128) = make_uint4(l[0], l[1], l[2], l[3]);
+          two_sum(sh[gi], sl[gi], t.x + t.y);
+          if (!X4) two_sum(qh[gi], ql[gi], pq.x + pq.y);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
