@@ -328,9 +328,11 @@ stats_status stats_set_grid_wait(stats_ctx* ctx, int64_t wait_ns, int32_t absent
 stats_status stats_set_wide_pairs(stats_ctx* ctx, int32_t pairs);
 
 /* Launch shape of the STATS_EXACT pass (-1 = the library's default for the ctx's converter):
- *   0  15 consumer warps, 64 rows each per stage (960-row stages)
- *   1  19 consumer warps, 32 rows each (608-row stages)
- *   2  23 consumer warps, 32 rows each (736-row stages)
+ *   0  15 consumer warps, 64 rows each per stage (960-row stages), mma.sync on those warps
+ *   1  19 consumer warps, 32 rows each (608-row stages), mma.sync
+ *   2  23 consumer warps, 32 rows each (736-row stages), mma.sync
+ *   3  14 converting warps, 64 rows each (896-row stages); the digit Gram on tcgen05 MMAs
+ *      issued by one thread, accumulated in tensor memory and read by four more warps
  * More warps hide more latency per SM but get fewer registers and smaller stages.  Results
  * do not depend on the shape (integer accumulation).  Errors: EINVAL (unknown shape, or the
  * ctx's rows do not fit that shape's pipeline). */

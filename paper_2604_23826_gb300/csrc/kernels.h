@@ -56,12 +56,17 @@ struct ExactParams {
   unsigned int* status;          // ctx sticky device status bits
 };
 
-// Launch shapes of the EXACT pass: consumer warps (plus one producer warp) and rows each
-// consumer takes per stage (a multiple of 32).  One block per SM; the register budget falls
-// with the thread count (128, 96 and 80 per thread for 16, 20 and 24 warps).
-constexpr int kExactShapes = 3;
-__host__ __device__ constexpr int exact_shape_warps(int shape) { return shape == 0 ? 15 : shape == 1 ? 19 : 23; }
-__host__ __device__ constexpr int exact_shape_rpw(int shape) { return shape == 0 ? 64 : 32; }
+// Launch shapes of the EXACT pass: converting warps (plus one producer warp) and rows each
+// takes per stage (a multiple of 32).  One block per SM; the register budget falls with the
+// thread count (128, 96 and 80 per thread for 16, 20 and 24 warps).  Shapes 0-2 multiply on
+// the converting warps (mma.sync); shape 3 hands the digits to tcgen05 MMAs issued by one
+// thread (plus an MMA warp and four tensor-memory reader warps: 20 warps, 96 registers).
+constexpr int kExactShapes = 4;
+__host__ __device__ constexpr int exact_shape_warps(int shape) {
+  return shape == 0 ? 15 : shape == 1 ? 19 : shape == 2 ? 23 : 14;
+}
+__host__ __device__ constexpr int exact_shape_rpw(int shape) { return (shape == 0 || shape == 3) ? 64 : 32; }
+__host__ __device__ constexpr bool exact_shape_tc(int shape) { return shape == 3; }
 constexpr int kExactMaxStages = 6;
 __host__ __device__ constexpr int exact_tile_rows(int shape) { return exact_shape_warps(shape) * exact_shape_rpw(shape); }
 // Bytes one column of `elem_bytes`-byte values takes in a stage of `tile` rows (128-byte granules).

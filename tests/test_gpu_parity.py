@@ -113,14 +113,14 @@ def test_exact_grid_chunk_and_repeat_invariance():
 
 
 @pytest.mark.parametrize("layout", [G.STATS_T1_L32, G.STATS_T1_L16])
-@pytest.mark.parametrize("n", [17, 607, 608, 737, 100_003, 1_000_003])
+@pytest.mark.parametrize("n", [5, 17, 607, 608, 737, 895, 897, 100_003, 1_000_003])
 def test_exact_launch_shapes_agree_with_oracle(layout, n):
     """Every launch shape of the exact pass (warps x rows per stage) against the oracle, ragged
-    sizes around the shapes' stage lengths (608, 736, 960 rows): bit-identical integer results."""
+    sizes around the shapes' stage lengths (608, 736, 896, 960 rows): bit-identical integer results."""
     cols = G.gen_table1(seed=11, nrows=n, layout=layout)
     st = O.stats_table1(11, n)
     raws = []
-    for shape in (0, 1, 2):
+    for shape in (0, 1, 2, 3):
         with _ctx(layout) as ctx:
             G.stats_set_exact_shape(ctx, shape)
             G.stats_accumulate(ctx, cols, n)
@@ -130,7 +130,37 @@ def test_exact_launch_shapes_agree_with_oracle(layout, n):
         assert r.S_exact == raws[0].S_exact and np.array_equal(r.S, raws[0].S) and np.array_equal(r.s, raws[0].s)
 
 
-@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("layout", [G.STATS_T1_L32, G.STATS_T1_L16])
+def test_exact_tcgen05_shape_grids_chunks_and_int32_flushes(layout):
+    """The tcgen05 shape (3) on one block (about 1100 stages: ~980 accumulation chains, so the
+    readers' int32 partial sums go to the int64 accumulator 15 times), on 3 and on 152 blocks,
+    and in uneven chunks, each a separate call: bit-identical to the oracle and to shape 0."""
+    n = 1_000_003
+    cols = G.gen_table1(seed=21, nrows=n, layout=layout)
+    st = O.stats_table1(21, n)
+    raws = []
+    for grid in (1, 3, 152):
+        with _ctx(layout) as ctx:
+            G.stats_set_exact_shape(ctx, 3)
+            G.stats_set_grid(ctx, grid)
+            G.stats_accumulate(ctx, cols, n)
+            raws.append(G.stats_raw(ctx))
+    with _ctx(layout) as ctx:
+        G.stats_set_exact_shape(ctx, 3)
+        edges = [0, 3, 899, 900, 17_000, 17_921, 500_000, n]
+        for a, b in zip(edges[:-1], edges[1:]):
+            G.stats_accumulate(ctx, [c[a:] for c in cols], b - a)
+        raws.append(G.stats_raw(ctx))
+    with _ctx(layout) as ctx:
+        G.stats_set_exact_shape(ctx, 0)
+        G.stats_accumulate(ctx, cols, n)
+        raws.append(G.stats_raw(ctx))
+    _check_exact(raws[0], st)
+    for r in raws[1:]:
+        assert r.n == raws[0].n and r.S_exact == raws[0].S_exact and np.array_equal(r.s, raws[0].s)
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
 def test_exact_launch_shapes_generic_and_unaligned(shape):
     """The generic converter in every shape, on aligned and unaligned columns (plain loads)."""
     rng = np.random.default_rng(13)
@@ -156,7 +186,7 @@ def test_exact_launch_shapes_generic_and_unaligned(shape):
                 assert res[1].S_exact[j][k] == st.S[j][k]
     with G.stats_init(cfg) as ctx:
         with pytest.raises(G.StatsError):
-            G.stats_set_exact_shape(ctx, 3)
+            G.stats_set_exact_shape(ctx, 4)
 
 
 def test_exact_merge_export_import():
