@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
     ap.add_argument("--exact-shape", type=int, default=-1,
-                    help="launch shape of the exact pass (-1: the library default; 0, 1, 2: stats.h)")
+                    help="launch shape of the exact pass (-1: the library default; 0-3: stats.h)")
     ap.add_argument("--workload", choices=("table1", "tables4096", "wide256", "f32table", "table1_1e10", "table1_file",
                                                 "table1_csv"),
                     default="table1",
@@ -517,7 +517,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         pass
     traffic = None
     if (NCU_TRAFFIC["bytes_per_row"] and NCU_TRAFFIC["src_hash"] == kernel_src_hash()
-            and NCU_TRAFFIC["layout"] == args.layout):
+            and NCU_TRAFFIC["layout"] == args.layout and args.exact_shape in (-1, 0)):
         traffic = NCU_TRAFFIC["bytes_per_row"] * n
     out = {
         "metric": METRIC, "value": world * n / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
@@ -533,7 +533,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "statistics, then the analysis of the whole table" if world > 1 else "")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "traffic": traffic,
-                     "kernel": "exact_pass_kernel<ConvT1>", "kernel_ms": kernel_ms,
+                     "kernel": ("exact_tc_kernel<ConvT1> (tcgen05)" if args.exact_shape == 3 else
+                                "exact_pass_kernel<ConvT1>"), "kernel_ms": kernel_ms,
                      "algorithmic_bytes": n * bpr,
                      "peak_nominal": 8000.0, "frac_nominal": achieved / 8000.0,
                      "peak_read_only_measured": read_peak,
