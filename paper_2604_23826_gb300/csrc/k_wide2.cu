@@ -208,7 +208,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer (leader)
+    // ---------------------------------------------------------------- MMA issuer (leader) / relay (peer)
+    if (!leader && lane == 0) {
+      // the peer's epilogue warps arrive on local barriers; this thread forwards each drained
+      // chain to the leader (one cluster-scope arrive per chain)
+      const uint32_t remote0 = cluster_addr(&d_empty[0], 0);
+      int b = 0;
+      uint32_t ph = 0;
+      for (int64_t k = 0; k < nchains; ++k) {
+        if (!tc05::wait_live(&r_epi[b], ph, &s_dead)) {
+          record_timeout(&s_dead, P.status);
+          break;
+        }
+        arrive_cluster(remote0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
+        if (++b == 2) {
+          b = 0;
+          ph ^= 1u;
+        }
+      }
+    }
     if (leader) {
       int s = 0, bd = 0;
       uint32_t ph = 0, phd = 0;
@@ -269,27 +287,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
     __syncwarp();
   } else if (warp == 2 || warp == 3) {
     // ---------------------------------------------------------------- relays (peer CTA)
-    // The peer's converter (warp 2) and epilogue (warp 3) warps arrive on local barriers; one
-    // thread forwards each completed phase to the leader with a single cluster-scope arrive,
-    // so the working warps never wait on a cluster-wide release themselves.
+    // The peer's converter warps arrive on local barriers; one thread forwards each completed
+    // phase to the leader with a single cluster-scope arrive, so the converters never wait on a
+    // cluster-wide release themselves.  A release at cluster scope costs about a stage's time
+    // under load, so two threads take alternate stages (warp 2 the even ones, warp 3 the odd).
     if (!leader && lane == 0) {
-      const bool conv = warp == 2;
-      uint64_t* local = conv ? r_conv : r_epi;
-      const uint32_t remote0 = cluster_addr(conv ? &c_full[0] : &d_empty[0], 0);
-      const int nb = conv ? kPStages : 2;
-      const int64_t count = conv ? my : nchains;
-      int b = 0;
-      uint32_t ph = 0;
-      for (int64_t k = 0; k < count; ++k) {
-        if (!tc05::wait_live(&local[b], ph, &s_dead)) {
+      const uint32_t remote0 = cluster_addr(&c_full[0], 0);
+      for (int64_t k = warp - 2; k < my; k += 2) {
+        const int b = static_cast<int>(k % kPStages);
+        if (!tc05::wait_live(&r_conv[b], static_cast<uint32_t>((k / kPStages) & 1), &s_dead)) {
           record_timeout(&s_dead, P.status);
           break;
         }
         arrive_cluster(remote0 + static_cast<uint32_t>(b * sizeof(uint64_t)));
-        if (++b == nb) {
-          b = 0;
-          ph ^= 1u;
-        }
       }
     }
   } else if (warp >= 4 && warp < 4 + kPConv) {
