@@ -25,14 +25,16 @@
 //   warp 1      tensor memory (allocated by both CTAs together) and, in the leader, the MMA
 //               issuer: it waits until both CTAs have converted the stage and drained the
 //               accumulator buffer, issues the stage's MMAs, and commits to the stage-free and
-//               (at a chain's end) chain-done barriers of both CTAs (multicast);
-//   warps 2-3   in the peer, relays: its converter and epilogue warps arrive on local
-//               barriers, and one thread forwards each completed phase to the leader with a
-//               single cluster-scope arrive (a release at cluster scope stalls the arriving
-//               thread until its writes are visible to the pair);
+//               (at a chain's end) chain-done barriers of both CTAs (multicast); in the peer,
+//               one thread relays the epilogue's drained chains to the leader;
+//   warps 2-3   in the peer, relays of converted stages (warp 2 the even stages, warp 3 the
+//               odd): the converter warps arrive on local barriers, and a relay thread forwards
+//               each completed phase to the leader with a single cluster-scope arrive (a release
+//               at cluster scope stalls the arriving thread for about a stage's time under load,
+//               so no converter pays it, and one thread alone could not keep up);
 //   warps 4-7   converters: the stage's FP32 becomes, in place, the K-major core matrices of h
-//               and l (or 2l), four 8-column groups per warp in turn; column sums of r and (BF16x3)
-//               sums of l^2;
+//               and l (or 2l), four 8-column groups per warp, two at a time; column sums of r
+//               and (BF16x3) sums of l^2;
 //   warps 8-15  epilogue: two warps per TMEM lane quarter, 128 columns each; every chain is
 //               added into FP32 registers (round to nearest), and every flush into (hi, lo)
 //               pairs in the CTA's slot.
