@@ -23,8 +23,8 @@
 // multiple apart, with P >= 32, takes one 2D tensor copy per stage (zeros past p);
 // otherwise one bulk copy (cp.async.bulk, mbarrier completion) per column (4-8 KB
 // for P <= 16), and columns sit RS + 16 floats apart, so that the consumers'
-// 128-bit loads are free of bank conflicts.  Seven consumer warps take the 16-row
-// K blocks in turn.  Lane
+// 128-bit loads are free of bank conflicts.  Consumer warps (15 for up to 32 columns,
+// 7 for 64) take the 16-row K blocks in turn.  Lane
 // (g, t) reads rows 4t..4t+3 of columns g + 8m with one 128-bit load per m;
 // those four rows fill the k slots (2t, 2t+1, 2t+8, 2t+9) of both the A
 // fragment (m16n8k16, A = X^T: rows = columns of X) and the B fragment
@@ -59,8 +59,6 @@ namespace ss {
 
 namespace {
 
-constexpr int kGC = kGram32Warps;          // consumer warps
-constexpr int kGThreads = 32 * (kGC + 1);  // + one producer warp
 template <int P>
 struct G32 {
   // P >= 32: 240-row stages, filled by one 2D tensor copy when the table's columns are
@@ -73,7 +71,11 @@ struct G32 {
   static constexpr int LDC = TMAP ? RS : RS + 16;   // column stride in floats (= 16 mod 32)
   static constexpr int SF = P * LDC;                // floats per stage
   static constexpr int KBS = RS / 16;
-  static constexpr int UNROLL = P <= 8 ? 4 : P <= 32 ? 2 : 1;  // independent K blocks in flight per warp         // K blocks per stage
+  // consumer warps (plus one producer warp): 15 for up to 32 columns, whose fragments fit the
+  // 128 registers of a 512-thread block; 7 for 64 columns, which need ~255
+  static constexpr int GC = P <= 32 ? kGram32Warps : 7;
+  static constexpr int THREADS = 32 * (GC + 1);
+  static constexpr int UNROLL = P <= 8 ? 4 : P <= 16 ? 2 : 1;  // independent K blocks in flight per warp
   static constexpr int NM = P / 8;            // column groups of a lane: columns g + 8m
   static constexpr int NI = P >= 16 ? P / 16 : 1;
   static constexpr int NJ = P / 8;
@@ -143,7 +145,8 @@ __device__ __forceinline__ void add_slots(const float2* __restrict__ slots, int 
 }
 
 // consumer warps only (named barrier 1)
-__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kGC) : "memory"); }
+template <int GC>
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * GC) : "memory"); }
 
 // bounded wait that also gives up once another warp of the CTA has recorded a failure
 __device__ __forceinline__ bool wait_live(uint64_t* bar, uint32_t parity, volatile unsigned int* dead) {
@@ -249,7 +252,7 @@ __device__ __forceinline__ void mma_kblock(const Frag<P>& F, const float (&z)[4]
 }
 
 template <int P, bool X4>
-__global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_constant__ Gram32Launch L) {
+__global__ void __launch_bounds__(G32<P>::THREADS, 1) gram32_kernel(const __grid_constant__ Gram32Launch L) {
   using C = G32<P>;
   constexpr int RS = C::RS, LDC = C::LDC, SF = C::SF, NJ = C::NJ, E = C::E, TILES = C::TILES;
   extern __shared__ __align__(128) float ring[];
@@ -263,19 +266,19 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x, b = blockIdx.x;
-  for (int i = threadIdx.x; i < L.ntables; i += kGThreads) s_stage0[i] = L.tabs[i].stage0;
+  for (int i = threadIdx.x; i < L.ntables; i += C::THREADS) s_stage0[i] = L.tabs[i].stage0;
   if (threadIdx.x == 0) {
     s_stage0[L.ntables] = L.total_stages;
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kGC);
+      mbar_init(&empty[s], C::GC);
     }
     s_dead = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kGC) {
+  if (warp == C::GC) {
     // ------------------------------------------------------------------ producer
     // the stages of all tables in order, dealt in chunks of L.chunk stages round-robin
     // to the CTAs: neighbouring CTAs read neighbouring row ranges of a large table,
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
 #pragma unroll
   for (int i = 0; i < 4; ++i) asm volatile("mov.b32 %0, 0;" : "=f"(zq[i]));
   float2* scratch = reinterpret_cast<float2*>(L.warp_scratch) +
-                    (static_cast<size_t>(b) * kGC + warp) * (E * 32);
+                    (static_cast<size_t>(b) * C::GC + warp) * (E * 32);
   int s = 0;
   uint32_t ph = 0;
   bool dead = false;
@@ -410,11 +413,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
     } while (gs >= s_stage0[ti + 1]);
     const Gram32Table& T = L.tabs[ti];
     const int p = T.p;
-    for (int c = threadIdx.x; c < P; c += 32 * kGC) {
+    for (int c = threadIdx.x; c < P; c += 32 * C::GC) {
       const float v = c < p ? -__ldg(T.shift + c) : 0.f;
       s_npiv[c] = make_float2(v, v);
     }
-    consumers_sync();
+    consumers_sync<C::GC>();
     float acc[TILES][4];
     float2 sum[C::NM], lsq[C::NM];
 #pragma unroll
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
       fresh = false;
     };
 
-    int rot = 0;  // K blocks of this run before the current stage, mod kGC
+    int rot = 0;  // K blocks of this run before the current stage, mod C::GC
     const int end = s_stage0[ti + 1];
     for (; gs < end && gs < L.total_stages; (++gs == (ch + 1) * L.chunk) ? (ch += G, gs = ch * L.chunk) : 0) {
       if (!dead && !wait_live(&full[s], ph, &s_dead)) {
@@ -468,21 +471,21 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
       if (!dead) {
         const int rows = s_rows[s];
         const float* st = ring + s * SF;
-        // K blocks kb0, kb0 + kGC, ...: the run's K block (stage * KBS + kb) = warp mod kGC
-        const int kb0 = (warp - rot + kGC) % kGC;
+        // K blocks kb0, kb0 + C::GC, ...: the run's K block (stage * KBS + kb) = warp mod C::GC
+        const int kb0 = (warp - rot + C::GC) % C::GC;
         const int nkb = (rows + 15) >> 4;  // a ragged last K block is padded with the pivot
         int done = 0, kb = kb0;
         constexpr int U = C::UNROLL;
 #pragma unroll 1
-        for (; kb + (U - 1) * kGC < nkb; kb += U * kGC, done += U) {
+        for (; kb + (U - 1) * C::GC < nkb; kb += U * C::GC, done += U) {
           Frag<P> F[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u) convert_kblock<P, X4>(st, kb + u * kGC, g, t, s_npiv, sum, lsq, F[u]);
+          for (int u = 0; u < U; ++u) convert_kblock<P, X4>(st, kb + u * C::GC, g, t, s_npiv, sum, lsq, F[u]);
 #pragma unroll
           for (int u = 0; u < U; ++u) mma_kblock<P, X4>(F[u], zq, acc);
         }
 #pragma unroll 1
-        for (; kb < nkb; kb += kGC, ++done) {
+        for (; kb < nkb; kb += C::GC, ++done) {
           Frag<P> F;
           convert_kblock<P, X4>(st, kb, g, t, s_npiv, sum, lsq, F);
           mma_kblock<P, X4>(F, zq, acc);
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
           since = 0;
           flush();
         }
-        rot = (rot + C::KBS) % kGC;
+        rot = (rot + C::KBS) % C::GC;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -505,7 +508,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
     // after mid-run flushes, the pairs in scratch) added in warp order through a shared
     // buffer, one warp at a time (eight words per step, their loads issued together)
     float2* __restrict__ red = reinterpret_cast<float2*>(ring + C::STAGES * SF) + lane;
-    for (int w = 0; w < kGC; ++w) {
+    for (int w = 0; w < C::GC; ++w) {
       if (warp == w) {
         constexpr int B = 8;
 #pragma unroll
@@ -539,13 +542,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gram32_kernel(const __grid_const
           }
         }
       }
-      consumers_sync();
+      consumers_sync<C::GC>();
     }
     const int sid = static_cast<int>(((b - s_stage0[ti] / L.chunk) % G + G) % G);
     float2* cslot = reinterpret_cast<float2*>(T.slots) + static_cast<size_t>(sid) * (E * 32);
     const float2* redb = reinterpret_cast<const float2*>(ring + C::STAGES * SF);
-    for (int i = threadIdx.x; i < E * 32; i += 32 * kGC) __stcg(cslot + i, redb[i]);
-    consumers_sync();  // the buffer is free for the next run
+    for (int i = threadIdx.x; i < E * 32; i += 32 * C::GC) __stcg(cslot + i, redb[i]);
+    consumers_sync<C::GC>();  // the buffer is free for the next run
   }
 }
 
@@ -602,7 +605,7 @@ cudaError_t launch_p(const Gram32Launch& L, int grid, cudaStream_t st) {
   const int smem = G32<P>::STAGES * G32<P>::SF * 4 + G32<P>::E * 32 * 8;  // ring + reduction buffer
   cudaError_t e = cudaFuncSetAttribute(gram32_kernel<P, X4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  gram32_kernel<P, X4><<<grid, kGThreads, smem, st>>>(L);
+  gram32_kernel<P, X4><<<grid, G32<P>::THREADS, smem, st>>>(L);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // merge: entries of a table spread over `parts` blocks, at least ~2 blocks per SM in all

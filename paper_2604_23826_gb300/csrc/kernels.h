@@ -142,7 +142,7 @@ cudaError_t launch_split_batched(const SplitParams* tabs, const int2* units, int
 // stages of a list of tables; a small second launch adds each table's per-CTA
 // slots, in slot order, into its accumulators.
 // ---------------------------------------------------------------------------
-constexpr int kGram32Warps = 7;         // consumer warps per CTA (plus one producer warp)
+constexpr int kGram32Warps = 15;        // most consumer warps per CTA (plus one producer warp)
 constexpr int kGram32MaxTables = 4096;  // tables per launch
 struct Gram32Table {
   const float* const* cols;  // device array of p column pointers
