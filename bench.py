@@ -73,7 +73,7 @@ def parse_args():
     ap.add_argument("--p", type=int, default=64, help="f32table: columns")
     ap.add_argument("--ntables", type=int, default=4096)
     ap.add_argument("--wave-gb", type=float, default=64.0)
-    ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S")
+    ap.add_argument("--mode", default=None, help="tables4096 / wide256: BF16X3, BF16X4, FP32, FP64S; tables4096 also FP64")
     ap.add_argument("--tune", choices=("off", "cached", "measure"), default="off",
                     help="tables4096: batched-launch tuning (off: library defaults; cached: a cached choice for "
                          "this device and library build, measured first if there is none; measure: re-measure on "
@@ -553,9 +553,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     ctx.close()
 
 # ----------------------------------------------------------------------------- FP32 workloads
-MODE_NAMES = {"BF16X3": "STATS_BF16X3", "BF16X4": "STATS_BF16X4", "FP32": "STATS_FP32", "FP64S": "STATS_FP64_SHIFTED"}
+MODE_NAMES = {"BF16X3": "STATS_BF16X3", "BF16X4": "STATS_BF16X4", "FP32": "STATS_FP32", "FP64S": "STATS_FP64_SHIFTED",
+              "FP64": "STATS_FP64"}
 MODE_KERNEL = {"BF16X3": "split_kernel (mma.sync bf16)", "BF16X4": "split_kernel (mma.sync bf16)",
-               "FP32": "core_kernel<float>", "FP64S": "core_kernel<double>"}
+               "FP32": "core_kernel<float>", "FP64S": "core_kernel<double> (shifted; fp64 kernel for p <= 12)",
+               "FP64": "core_kernel<double> (raw moments, the paper's plain FP64 kernel; fp64 kernel for p <= 12)"}
 
 
 def _base_line(args, world, metric, value, ms_per_step, config, roofline, clocks, launches, extra):
@@ -615,8 +617,10 @@ def run_tables(args, rank: int, world: int, local_rank: int):
             G.stats_reset(ctxs[t])
     wave_ms = []
     host_ms = []
-    # per wave: one pivot launch + one batched launch per tile width present (32: p <= 32, 64: p = 64)
-    launches_per_step = sum(1 + len({32 if params[t][1] <= 32 else 64 for t in g}) for g in groups)
+    # per wave: one pivot launch + one batched launch per tile width present (32: p <= 32, 64: p = 64);
+    # the CUDA-core modes run one pass per table (shifted: after its pivot launch)
+    launches_per_step = (sum(1 + len({32 if params[t][1] <= 32 else 64 for t in g}) for g in groups)
+                         if mode_name.startswith("BF16") else len(mine) * (1 if mode_name == "FP64" else 2))
 
     def step(record: bool):
         for t in mine:
