@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--layout", choices=("L32", "L16"), default="L32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-detail", action="store_true",
+                    help="cpu_baseline also times the oracle with one thread and the histogram oracle at n = 1e10")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--chunk-rows", type=int, default=1 << 24)
     ap.add_argument("--exact-shape", type=int, default=-1,
@@ -271,6 +273,27 @@ def oracle_sample(seconds: float, row0: int = 0):
     _, cov, _ = O.analysis_from_stats(st)
     O.jacobi(cov)
     return n, time.perf_counter() - t0, threads
+
+
+def oracle_detail(threads: int) -> dict:
+    """The oracle's rates on the host cores: the per-row oracle at n = 1e6 with all threads and
+    with one, and the exact histogram oracle (a count-only pass over the 6000 (B, C, D) cells)
+    on the n = 1e10 table with all threads, its closed forms checked."""
+    import oracle as O
+    out = {}
+    for th in (threads, 1):
+        t0 = time.perf_counter()
+        O.stats_table1(SEED, 1_000_000, threads=th)
+        dt = time.perf_counter() - t0
+        out[f"per_row_n1e6_threads{th}"] = {"rows_per_s": 1e6 / dt, "s": dt}
+    n10 = 10**10
+    t0 = time.perf_counter()
+    st = O.stats_table1_hist(2, n10, threads=threads)
+    dt = time.perf_counter() - t0
+    out["histogram_n1e10"] = {"rows_per_s": n10 / dt, "s": dt, "threads": threads,
+                              "closed_forms": bool(st.n == n10 and st.s[0] == n10 * (n10 + 1) // 2 and
+                                                   st.S[0][0] == n10 * (n10 + 1) * (2 * n10 + 1) // 6)}
+    return out
 
 
 def run_reference(args, rank: int):
@@ -503,6 +526,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         cpu = {"value": rows / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{rows} Table 1 rows (seed {SEED}) of the {n}-row workload: per-row exact "
                          f"__int128/double-double sums, exact centering, Jacobi; {secs:.1f} s"}
+        if args.oracle_detail:
+            cpu["detail"] = oracle_detail(threads)
 
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
