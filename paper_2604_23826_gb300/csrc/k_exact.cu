@@ -502,12 +502,12 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) exact_pass_kernel(const __gri
 // ---- the tcgen05 form (launch shape 3) ----
 // Each of kTcW converting warps turns its 64 rows of a stage into digits (in registers, which
 // frees the stage for the next bulk copy), then, once the previous stage's MMA on its slot
-// has completed, stores them in its own 4 KB operand slot: four sets of 16 rows side by side, slot
-// row k (0..15) holding the 128 digits [set 0 | set 1 | set 2 | set 3] of stage rows
+// has completed, stores them in its own 4 KB operand slot: four sets of 16 rows side by side,
+// slot row k (0..15) holding the 128 digits [set 0 | set 1 | set 2 | set 3] of stage rows
 // 64 w + 16 b + k.  When every slot of the stage is stored, one thread issues per slot
-// (each followed by a commit that frees that slot) D += S^T S (M = N = 128, K = 16, f16 operands read MN-major, FP32 in tensor memory): the
-// diagonal 32 x 32 block b of D is the digit Gram of set b; the off-diagonal blocks (products
-// of different rows) are never read.  A stage is one accumulation chain (kTcW slots:
+// D += S^T S (M = N = 128, K = 16, f16 operands read MN-major, FP32 in tensor memory), each
+// MMA followed by a commit that frees its slot: the diagonal 32 x 32 block b of D is the
+// digit Gram of set b; the off-diagonal blocks (products of different rows) are never read.  A stage is one accumulation chain (kTcW slots:
 // 16 kTcW = 224 rows per set, every partial sum an integer below 2^24, exact in FP32) into one
 // of two 128-column accumulators.  Four reader warps take the diagonal blocks of each finished
 // chain into int32 partial sums, every 64 chains into the block's int64 accumulator.
