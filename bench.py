@@ -44,6 +44,29 @@ BYTES_PER_ROW = {0: 60, 1: 44}
 NCU_TRAFFIC = {"bytes_per_row": 60.069, "src_hash": "1f417e2a986ce63b", "layout": "L32"}
 
 
+# DRAM traffic of the FP32 split passes (BF16x3) from one ncu capture each on a smaller case:
+# reads per algorithmic byte (they grow with the rows) plus the per-launch slot writes (fixed);
+# profiles/wide2_pairs_p256_bf16x3_n4e6.md and profiles/narrow_tcgen05_p64_bf16x3_n8e6.md.
+NCU_TRAFFIC_SPLIT = {
+    "wide2": {"read_per_byte": 4220192000 / 4096000000, "write_bytes": 126807296,
+              "files": ("k_wide2.cu", "tc05.cuh", "common.cuh"), "src_hash": "6c2a6506838f0ead"},
+    "narrow": {"read_per_byte": 2074298000 / 2048000000, "write_bytes": 31283200,
+               "files": ("k_narrow.cu", "tc05.cuh", "common.cuh"), "src_hash": "22da905282b4366e"},
+}
+
+
+def split_traffic(kind: str, algorithmic_bytes: int):
+    """Traffic of one split-pass launch scaled from its capture, or None if the sources changed."""
+    t = NCU_TRAFFIC_SPLIT[kind]
+    h = hashlib.sha256()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_2604_23826_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != t["src_hash"]:
+        return None
+    return t["read_per_byte"] * algorithmic_bytes + t["write_bytes"]
+
+
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
     for f in ("k_exact.cu", "common.cuh"):
@@ -729,6 +752,7 @@ def run_tables(args, rank: int, world: int, local_rank: int):
         mu32, sd32 = np.float32(mu).astype(np.float64), np.float32(sd).astype(np.float64)
         worst_mean_rel = max(worst_mean_rel, float(np.max(np.abs(an.mean - mu32) / sd32)) * math.sqrt(n))
     oracle_check = None
+    tables_cpu = None
     if args.oracle_check != "none" and rank == 0:
         # the same tables regenerated (same seeds, same values), copied back, and the oracle's
         # two-pass covariance compared with the batched pass's result
@@ -752,6 +776,10 @@ def run_tables(args, rank: int, world: int, local_rank: int):
                 err = float(np.linalg.norm(fin_of[t].cov - cov) / np.linalg.norm(cov))
                 if err >= worst:
                     worst, worst_t = err, t
+        tables_cpu = {"value": int(sum(params[t][0] for t in pick)) / max(o_secs, 1e-9), "unit": "rows/s",
+                      "cores": O.default_threads(), "kind": "oracle",
+                      "sample": f"the oracle's two-pass covariance (double-double) of {len(pick)} of the tables "
+                                f"({args.oracle_check} sample), {o_secs:.1f} s"}
         oracle_check = {"cov_rel_vs_oracle": worst, "tables": len(pick),
                         "rows": int(sum(params[t][0] for t in pick)),
                         "worst_table": {"index": worst_t, "n": params[worst_t][0], "p": params[worst_t][1]},
@@ -788,6 +816,7 @@ def run_tables(args, rank: int, world: int, local_rank: int):
     out = _base_line(args, world, "rows/s and HBM GB/s (% of roofline) for fused sums+XᵀX, batched FP32 tables",
                      rows_all / (ms_all / 1e3), ms_all, config, roof, clocks,
                      launches_per_step * args.steps, extra)
+    out["cpu_baseline"] = tables_cpu if world == 1 else None
     if rank == 0:
         print(json.dumps(out), flush=True)
     for c in ctxs.values():
@@ -878,6 +907,11 @@ def run_wide(args, rank: int, world: int, local_rank: int):
                 "rows": m, "cov_rel_vs_oracle": float(np.linalg.norm(an_m.cov - cov_o) / np.linalg.norm(cov_o)),
                 "top10_eval_rel_vs_oracle": float(np.max(np.abs(an_m.evals[:10] - ev_o) / ev_o)),
                 "oracle_s": o_secs, "sample": f"the table's first {m} rows on both sides"}
+    wide_cpu = None
+    if args.oracle_check != "none" and rank == 0 and world == 1:
+        wide_cpu = {"value": m / o_secs, "unit": "rows/s", "cores": O.default_threads(), "kind": "oracle",
+                    "sample": f"the oracle's two-pass covariance (double-double) of the table's first {m} rows, "
+                              f"{o_secs:.1f} s"}
     ref = results.get("FP64S")
     main_mode = modes[0]
     for mname, r in results.items():
@@ -892,7 +926,8 @@ def run_wide(args, rank: int, world: int, local_rank: int):
               "step": "one fused pass over the table", "l2": "inputs larger than L2 (no flush)",
               "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": m["GB_per_s"], "peak": peak, "unit": "GB/s", "frac": m["hbm_frac"],
-            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+            "traffic": split_traffic("wide2", 4 * p * n) if main_mode == "BF16X3" and 128 < p <= 256 else None,
             "kernel": (("wide2_kernel (tcgen05 cta_group::2, pairs of SMs, TMEM accumulators)" if 128 < p <= 256 else
                         "wide_kernel (tcgen05, TMEM accumulators)") if main_mode.startswith("BF16") else
                        MODE_KERNEL[main_mode]), "kernel_ms": m["ms"], "algorithmic_bytes": 4 * p * n,
@@ -905,6 +940,7 @@ def run_wide(args, rank: int, world: int, local_rank: int):
                      world * n / (t_ms.item() / 1e3), t_ms.item(), config, roof, clocks,
                      (3 if main_mode.startswith("BF16") else 2) * (args.steps if main_mode != "FP64S" else 1),
                      {"modes": results})
+    out["cpu_baseline"] = wide_cpu
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -961,7 +997,9 @@ def run_f32table(args, rank: int, world: int, local_rank: int):
               "step": "one fused pass over the table", "l2": "inputs larger than L2 (no flush)",
               "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+            "traffic": (split_traffic("narrow", 4 * p * n) if mode_name == "BF16X3" and 32 < p <= 64 and n >= (1 << 20)
+                        else None),
             "kernel": (("narrow_kernel (tcgen05, 33-64 columns)" if p > 32 and n >= (1 << 20) else
                         "gram32_kernel (register-fragment mma.sync bf16)") if p <= 64 and mode_name.startswith("BF16")
                        else MODE_KERNEL[mode_name]), "kernel_ms": ms, "algorithmic_bytes": 4 * p * n}
@@ -1025,7 +1063,9 @@ def run_table1_stream(args, rank: int, world: int, local_rank: int):
               "chunk_rows": chunk, "step": "exact pass over every chunk into one context (generation untimed)",
               "l2": "inputs larger than L2 (no flush)", "parallelism": f"rows sharded, {world} replica(s)"}
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "traffic": None,
+            "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+            "traffic": (NCU_TRAFFIC["bytes_per_row"] * n if NCU_TRAFFIC["src_hash"] == kernel_src_hash() and
+                        NCU_TRAFFIC["layout"] == args.layout else None),
             "kernel": "exact_pass_kernel<ConvT1>", "kernel_ms": ms, "algorithmic_bytes": n * bpr}
     out = _base_line(args, world, METRIC, world * n / (ms / 1e3), ms, config, roof,
                      {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (long chunked run)"]},
